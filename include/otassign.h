@@ -1,0 +1,177 @@
+/*
+ * otassign.h -- C ABI of libotassign.so, an exact GPU solver for the
+ * assignment problem on dense integer cost matrices (sm_103a).
+ *
+ * The problem (paper "A Study of Performance of Optimal Transport",
+ * Sec. 1, Eq. 1, with supplies r and demands c all ones): given an n x m cost
+ * matrix C (n <= m), find an injective map sigma: [n] -> [m] that minimises
+ * sum_i C[i][sigma(i)].  Two exact algorithms are offered:
+ *
+ *   OT_KM   Kuhn-Munkres (Hungarian) in shortest-augmenting-path form, one
+ *           root row at a time in index order (Sec. 2.3 "Variations of the
+ *           Hungarian algorithm", Sec. 4.1 "KM and variants").  With the
+ *           tie-breaks below its assignment and duals are deterministic and
+ *           identical to the CPU reference implementation.
+ *   OT_BKM  batched KM (Sec. 2.3 "Batched KM"): augmenting paths are routed
+ *           in batches along tight edges from all free rows at once and the
+ *           duals are adjusted across the cut between reached and unreached
+ *           vertices in the same manner as KM.  Exact mode (scaling factor 1):
+ *           its optimal cost equals OT_KM's; assignment and duals may differ
+ *           among optimal ones but always form a valid certificate.
+ *
+ * Results.  row_to_col[i] = sigma(i); cost = sum_i C[i][sigma(i)] (int64);
+ * duals u[n], v[m] (int64) with u_i + v_j <= C[i][j] for all (i, j),
+ * equality on matched pairs, v_j <= 0, v_j = 0 on unmatched columns and
+ * sum(u) + sum(v) = cost, which proves optimality by LP duality.
+ *
+ * Tie-breaks (the paper is silent): rows are rooted in index order (OT_KM),
+ * the minimum slack selects the lowest column index, a slack entry changes
+ * only on a strictly smaller value (OT_KM) or a smaller (value, row) pair
+ * (OT_BKM).
+ *
+ * Memory.  Every pointer argument may be a device pointer or a host pointer;
+ * the library asks the CUDA runtime which one it is.  Host inputs are copied
+ * to device staging owned by the context and host outputs are written back
+ * before the call returns.  With device pointers the call is asynchronous on
+ * `stream` (a cudaStream_t; NULL means the context's own stream) unless
+ * stated otherwise; the caller keeps ownership of all buffers and the
+ * library keeps no caller pointer after the call returns.  The cost matrix is
+ * row-major int32 with leading dimension ldc (elements, ldc >= m).
+ *
+ * Errors.  Every call returns OT_OK (0) or a negative OT_ERR_* code and
+ * never throws or aborts; ot_last_error_string() gives detail.  Device code
+ * never traps: device-side failures are reported in a status word.
+ */
+#ifndef OTASSIGN_H
+#define OTASSIGN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OT_OK 0
+#define OT_PENDING 1             /* ot_assign_poll: not finished yet */
+#define OT_ERR_ARG (-1)          /* null pointer, n < 0, n > m, ldc < m, bad algo */
+#define OT_ERR_OOM (-2)          /* device or host allocation failed */
+#define OT_ERR_BUDGET (-3)       /* serving: request can never fit the HBM budget */
+#define OT_ERR_TIMEOUT (-4)      /* a bounded device wait expired */
+#define OT_ERR_CUDA (-5)         /* a CUDA runtime call failed */
+#define OT_ERR_OVERFLOW (-6)     /* |C| too large for exact int64 duals */
+#define OT_ERR_UNSUPPORTED (-7)  /* size outside what this build handles */
+#define OT_ERR_TICKET (-8)       /* unknown or already collected ticket */
+
+#define OT_KM 0
+#define OT_BKM 1
+
+/* Per-solve counters, written by ot_assign_solve_stats. */
+typedef struct ot_stats {
+  int64_t steps;          /* dependent tree-growing steps (one argmin each) */
+  int64_t rows_scanned;   /* cost rows evaluated (each over the columns outside T) */
+  int64_t cost_bytes;     /* 4 x reduced costs evaluated: the algorithmic bytes */
+  int64_t phases;         /* KM: rows rooted; BKM: dual-adjust/augment phases */
+  int64_t augmentations;  /* augmenting paths applied */
+  int64_t init_bytes;     /* BKM row-reduction pass bytes (4*n*m), else 0 */
+  int64_t reserved[2];
+} ot_stats;
+
+typedef struct ot_config {
+  int32_t device;            /* CUDA device ordinal; -1 = current device */
+  int64_t hbm_budget_bytes;  /* serving arena = admission budget; 0 = 4 GiB */
+  int32_t max_inflight;      /* serving: max requests resident at once; 0 = 4096 */
+  int32_t wave_streams;      /* serving: streams used for overlapping waves; 0 = 4 */
+  const char* tune_file;     /* autotuner table (JSON-lines); NULL = built-in */
+} ot_config;
+
+typedef struct ot_ctx ot_ctx;
+
+/* Create / destroy a context (device buffers, streams, serving thread).
+ * cfg may be NULL.  Destroy waits for outstanding work. */
+int ot_ctx_create(ot_ctx** out, const ot_config* cfg);
+void ot_ctx_destroy(ot_ctx* ctx);
+const char* ot_last_error_string(const ot_ctx* ctx);
+
+/* Solve one instance.  C[n*ldc], row_to_col[n], cost[1], u[n], v[m].
+ * u and v may be NULL if the duals are not wanted.  n == 0 gives cost 0. */
+int ot_assign_solve(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int32_t m,
+                    int32_t algo, int32_t* row_to_col, int64_t* cost, int64_t* u,
+                    int64_t* v, void* stream);
+
+/* As ot_assign_solve, then synchronises and fills *stats (host pointer). */
+int ot_assign_solve_stats(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n,
+                          int32_t m, int32_t algo, int32_t* row_to_col, int64_t* cost,
+                          int64_t* u, int64_t* v, ot_stats* stats, void* stream);
+
+/* Synchronise the context's stream and return the counters of the most
+ * recent ot_assign_solve / ot_assign_solve_batched call on device pointers,
+ * summed over its instances; reserved[0] receives the number of kernel
+ * launches that call made.  *total is a host pointer. */
+int ot_last_call_stats(ot_ctx* ctx, ot_stats* total);
+
+/* Solve k independent instances in one launch set (multi-instance
+ * batching).  The array arguments are HOST arrays of length k; their
+ * elements (C[t], row_to_col[t], u[t], v[t]) are device pointers, or all host
+ * pointers.  cost[k] and status[k] follow the same rule as the element
+ * pointers (device or host).  Instances are bucketed by size onto
+ * warp-, CTA- or cluster-sized solver groups chosen by the autotuner table.
+ * status[t] = 0 on success or a negative OT_ERR_* code for that instance.
+ * Each instance's result is identical to solving it alone. */
+int ot_assign_solve_batched(ot_ctx* ctx, int32_t k, const int32_t* const* C,
+                            const int64_t* ldc, const int32_t* n, const int32_t* m,
+                            int32_t algo, int32_t* const* row_to_col, int64_t* cost,
+                            int64_t* const* u, int64_t* const* v, int32_t* status,
+                            void* stream);
+
+/* Serving (continuous batching).  submit copies C (host or device pointer)
+ * into the context's device arena when the request is admitted under the HBM
+ * budget; requests that arrive while others run are launched in overlapping
+ * waves.  The caller's C may be reused as soon as submit returns.  *ticket
+ * identifies the request.  OT_ERR_BUDGET if the request alone exceeds the
+ * budget. */
+int ot_assign_submit(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int32_t m,
+                     int32_t algo, uint64_t* ticket);
+
+/* Poll a ticket: OT_PENDING while running; OT_OK once finished, after
+ * copying the results into row_to_col[n], cost[1], u[n], v[m] (host or
+ * device pointers; u, v may be NULL); the ticket is then retired.  A
+ * negative code reports a failed request (also retiring it). */
+int ot_assign_poll(ot_ctx* ctx, uint64_t ticket, int32_t* row_to_col, int64_t* cost,
+                   int64_t* u, int64_t* v);
+
+/* Wait until every submitted request has finished (not collected). */
+int ot_assign_drain(ot_ctx* ctx);
+
+/* Serving counters (host pointer, 8 entries): submitted, admitted,
+ * completed, waves launched, max concurrent waves observed, bytes resident,
+ * budget bytes, requests refused. */
+int ot_serving_counters(ot_ctx* ctx, int64_t* out8);
+
+/* Autotuner: for every size bucket present in the given instances (device
+ * pointers, as in ot_assign_solve_batched), time each compiled group shape
+ * `repeats` times on exactly those instances and keep the fastest shape for
+ * that bucket and algorithm in the context's table (also appended to
+ * cfg->tune_file when one was given).  Results are written to scratch and
+ * discarded.  Returns OT_OK or an error code. */
+int ot_autotune(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* ldc,
+                const int32_t* n, const int32_t* m, int32_t algo, int32_t repeats);
+
+/* Current table entry: shape (threads per instance, columns per thread)
+ * used for instances with m in the bucket that contains `m`. */
+int ot_tune_lookup(ot_ctx* ctx, int32_t algo, int32_t m, int32_t* threads_per_instance,
+                   int32_t* cols_per_thread);
+
+/* Force the table entry for the bucket containing m (tests, experiments).
+ * OT_ERR_UNSUPPORTED if the shape is not compiled in or cannot hold the
+ * bucket's widest instance. */
+int ot_tune_set(ot_ctx* ctx, int32_t algo, int32_t m, int32_t threads_per_instance,
+                int32_t cols_per_thread);
+
+/* Library version string, e.g. "otassign 0.1 sm_103a". */
+const char* ot_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OTASSIGN_H */

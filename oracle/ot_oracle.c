@@ -125,6 +125,7 @@ int64_t oracle_km(const int32_t *C, int64_t ldc, int n, int m,
         if (in_tree[j]) { u[col_to_row[j]] += delta; v[j] -= delta; }
         else slack[j] -= delta;
       }
+      if (jstar < 0) break;   /* unreachable for n <= m: some column is outside T */
       in_tree[jstar] = 1;
       if (col_to_row[jstar] < 0) jfree = jstar;
       else i = col_to_row[jstar];

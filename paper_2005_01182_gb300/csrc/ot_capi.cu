@@ -1,0 +1,746 @@
+// C ABI of libotassign.so: context, single and multi-instance solves,
+// bucketing scheduler, CUDA-graph replay and the autotuner.  The serving
+// loop lives in ot_serve.cu.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "otassign.h"
+#include "ot_ctx.h"
+#include "ot_group.cuh"
+#include "ot_shapes.h"
+
+namespace ot {
+cudaError_t launch_group_km(GroupShape, const Instance*, const int32_t*, int, int*, int, int, int,
+                            cudaStream_t);
+cudaError_t launch_group_bkm(GroupShape, const Instance*, const int32_t*, int, int*, int, int, int,
+                             cudaStream_t);
+
+cudaError_t launch_group(GroupShape shape, int algo, const Instance* insts, const int32_t* order,
+                         int num, int* work, int nmax, int mmax, int max_ctas,
+                         cudaStream_t stream) {
+  if (algo == kAlgoKM)
+    return launch_group_km(shape, insts, order, num, work, nmax, mmax, max_ctas, stream);
+  return launch_group_bkm(shape, insts, order, num, work, nmax, mmax, max_ctas, stream);
+}
+
+static const GroupShape kShapes[OT_NUM_GROUP_SHAPES] = {
+#define OT_ROW(IDX, TPI_, K_) GroupShape{TPI_, K_},
+    OT_GROUP_SHAPES(OT_ROW)
+#undef OT_ROW
+};
+
+int num_group_shapes() { return OT_NUM_GROUP_SHAPES; }
+GroupShape group_shape(int idx) { return kShapes[idx]; }
+
+size_t group_smem_bytes(GroupShape s, int algo, int nmax, int mmax) {
+  return group_bytes(s.tpi, algo, nmax, mmax) * (s.tpi == 32 ? 8 : 1);
+}
+
+size_t group_smem_limit() { return 227 * 1024; }
+
+int shape_index(int tpi, int k) {
+  for (int i = 0; i < OT_NUM_GROUP_SHAPES; ++i)
+    if (kShapes[i].tpi == tpi && kShapes[i].k == k) return i;
+  return -1;
+}
+
+int bucket_of(int m) {
+  int b = 0;
+  while (b < kNumBuckets - 1 && m > (32 << b)) ++b;
+  return b;
+}
+
+void default_table(int table[2][kNumBuckets]) {
+  // bucket b holds m <= 32 << b
+  static const int tpi[kNumBuckets] = {32, 32, 32, 32, 128, 256, 512, 1024};
+  static const int kk[kNumBuckets] = {1, 2, 4, 8, 4, 4, 4, 4};
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < kNumBuckets; ++b) table[a][b] = shape_index(tpi[b], kk[b]);
+}
+
+}  // namespace ot
+
+using namespace ot;
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+
+int ctx_fail(ot_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int ctx_cuda(ot_ctx* ctx, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return OT_OK;
+  return ctx_fail(ctx, OT_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool ptr_on_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int DevBuf::reserve(size_t bytes) {
+  if (bytes <= cap) return OT_OK;
+  const size_t want = std::max(bytes, cap * 2);
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  cap = 0;
+  if (cudaMalloc(&ptr, want) != cudaSuccess) {
+    cudaGetLastError();
+    ptr = nullptr;
+    return OT_ERR_OOM;
+  }
+  cap = want;
+  ++generation;
+  return OT_OK;
+}
+
+void DevBuf::release() {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  cap = 0;
+}
+
+int PinBuf::reserve(size_t bytes) {
+  if (bytes <= cap) return OT_OK;
+  const size_t want = std::max(bytes, cap * 2);
+  if (ptr) cudaFreeHost(ptr);
+  ptr = nullptr;
+  cap = 0;
+  if (cudaHostAlloc(&ptr, want, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    ptr = nullptr;
+    return OT_ERR_OOM;
+  }
+  cap = want;
+  return OT_OK;
+}
+
+void PinBuf::release() {
+  if (ptr) cudaFreeHost(ptr);
+  ptr = nullptr;
+  cap = 0;
+}
+
+static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ---------------------------------------------------------------------------
+// device-pointer batch: bucket, upload descriptors, launch (optionally as a
+// cached CUDA graph)
+// ---------------------------------------------------------------------------
+
+struct Bucket {
+  int shape;
+  int nmax = 0, mmax = 0;
+  std::vector<int> idx;
+};
+
+// insts[t] already holds device pointers; entries with skip[t] set are not
+// launched.  Writes per-instance stats into ctx->d_stats (k x 8).
+int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts,
+                     const std::vector<int>& skip, int algo, cudaStream_t stream, bool fork,
+                     bool own_stats, std::vector<int>* unsupported) {
+  const int k = int(insts.size());
+  if (own_stats) {
+    if (int rc = slot.d_stats.reserve(size_t(k) * 8 * sizeof(int64_t)); rc) return ctx_fail(ctx, rc, "stats alloc");
+    int64_t* dstats = static_cast<int64_t*>(slot.d_stats.ptr);
+    for (int t = 0; t < k; ++t) insts[t].stats = dstats + size_t(t) * 8;
+  }
+
+  // bucket by tuned shape
+  std::map<int, Bucket> buckets;
+  for (int t = 0; t < k; ++t) {
+    if (skip[t]) continue;
+    const Instance& I = insts[t];
+    int sh = ctx->table[algo][bucket_of(I.m)];
+    if (sh >= 0 && group_shape(sh).max_cols() < I.m) {
+      int def[2][kNumBuckets];
+      default_table(def);
+      sh = def[algo][bucket_of(I.m)];
+    }
+    if (I.m > kMaxGroupCols || sh < 0 ||
+        group_smem_bytes(group_shape(sh), algo, I.n, I.m) > group_smem_limit()) {
+      if (unsupported) unsupported->push_back(t);
+      continue;
+    }
+    Bucket& b = buckets[sh];
+    b.shape = sh;
+    b.nmax = std::max(b.nmax, I.n);
+    b.mmax = std::max(b.mmax, I.m);
+    b.idx.push_back(t);
+  }
+  // a shape may serve several m-buckets; keep the smem bound feasible
+  for (auto& kv : buckets) {
+    Bucket& b = kv.second;
+    std::sort(b.idx.begin(), b.idx.end(), [&](int a, int c) {
+      long long wa = (long long)insts[a].n * insts[a].m, wc = (long long)insts[c].n * insts[c].m;
+      return wa != wc ? wa > wc : a < c;
+    });
+  }
+  const int nb = int(buckets.size());
+  const size_t desc_bytes = al256(sizeof(Instance) * k);
+  const size_t order_bytes = al256(sizeof(int32_t) * (k + 1));
+  const size_t work_bytes = al256(sizeof(int) * (nb + 1));
+  const size_t total = desc_bytes + order_bytes + work_bytes;
+
+  // the pinned mirror may still feed the previous call's copy
+  if (slot.meta_pending) {
+    cudaEventSynchronize(slot.meta_ev);
+    slot.meta_pending = false;
+  }
+  if (int rc = slot.h_meta.reserve(total); rc) return ctx_fail(ctx, rc, "pinned alloc");
+  const int gen = slot.d_meta.generation;
+  if (int rc = slot.d_meta.reserve(total); rc) return ctx_fail(ctx, rc, "meta alloc");
+  if (slot.d_meta.generation != gen) slot.clear_graphs();
+
+  char* h = static_cast<char*>(slot.h_meta.ptr);
+  char* d = static_cast<char*>(slot.d_meta.ptr);
+  std::memcpy(h, insts.data(), sizeof(Instance) * k);
+  int32_t* horder = reinterpret_cast<int32_t*>(h + desc_bytes);
+  int* hwork = reinterpret_cast<int*>(h + desc_bytes + order_bytes);
+  std::memset(hwork, 0, work_bytes);
+  std::string key = std::to_string(algo) + "|" + std::to_string(k);
+  std::vector<int> offs;
+  int off = 0;
+  for (auto& kv : buckets) {
+    Bucket& b = kv.second;
+    offs.push_back(off);
+    for (int t : b.idx) horder[off++] = t;
+    key += "|" + std::to_string(b.shape) + "," + std::to_string(b.idx.size()) + "," +
+           std::to_string(b.nmax) + "," + std::to_string(b.mmax);
+  }
+  key += "|" + std::to_string(reinterpret_cast<uintptr_t>(stream));
+
+  const Instance* dinst = reinterpret_cast<const Instance*>(d);
+  const int32_t* dorder = reinterpret_cast<const int32_t*>(d + desc_bytes);
+  int* dwork = reinterpret_cast<int*>(d + desc_bytes + order_bytes);
+
+  auto enqueue = [&](cudaStream_t s) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(d, h, total, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (nb == 1 || !fork) {
+      int bi = 0;
+      for (auto& kv : buckets) {
+        Bucket& b = kv.second;
+        e = launch_group(group_shape(b.shape), algo, dinst, dorder + offs[bi], int(b.idx.size()),
+                         dwork + bi, b.nmax, b.mmax, 0, s);
+        if (e != cudaSuccess) return e;
+        ++bi;
+      }
+      return cudaSuccess;
+    }
+    if ((e = cudaEventRecord(ctx->fork_ev, s)) != cudaSuccess) return e;
+    int bi = 0;
+    for (auto& kv : buckets) {
+      Bucket& b = kv.second;
+      cudaStream_t bs = ctx->bstreams[bi % kForkStreams];
+      if ((e = cudaStreamWaitEvent(bs, ctx->fork_ev, 0)) != cudaSuccess) return e;
+      e = launch_group(group_shape(b.shape), algo, dinst, dorder + offs[bi], int(b.idx.size()),
+                       dwork + bi, b.nmax, b.mmax, 0, bs);
+      if (e != cudaSuccess) return e;
+      ++bi;
+    }
+    for (int s2 = 0; s2 < std::min(nb, kForkStreams); ++s2) {
+      if ((e = cudaEventRecord(ctx->join_ev[s2], ctx->bstreams[s2])) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(s, ctx->join_ev[s2], 0)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+
+  cudaError_t e = cudaSuccess;
+  if (nb == 0) {
+    // nothing to launch
+  } else if (slot.use_graphs) {
+    auto it = slot.graphs.find(key);
+    if (it == slot.graphs.end()) {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t e1 = enqueue(stream);
+        e = cudaStreamEndCapture(stream, &g);
+        if (e1 != cudaSuccess) e = e1;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e == cudaSuccess) {
+        if (slot.graphs.size() >= 64) slot.clear_graphs();
+        it = slot.graphs.emplace(key, ge).first;
+      }
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(it->second, stream);
+  } else {
+    e = enqueue(stream);
+  }
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "batch launch");
+  if (nb > 0) {
+    cudaEventRecord(slot.meta_ev, stream);
+    slot.meta_pending = true;
+  }
+  slot.last_launches = nb;
+  return OT_OK;
+}
+
+// Validate one instance's sizes.
+static int check_sizes(const void* C, int64_t ldc, int n, int m) {
+  if (n < 0 || m < 0 || n > m) return OT_ERR_ARG;
+  if (n > 0 && (!C || ldc < m)) return OT_ERR_ARG;
+  return OT_OK;
+}
+
+// Solve k instances; every pointer is either device (dev=true) or host.
+static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t* ldc,
+                      const int32_t* n, const int32_t* m, int algo, int32_t* const* r2c,
+                      int64_t* cost, int64_t* const* u, int64_t* const* v, int32_t* status,
+                      cudaStream_t stream, ot_stats* stats_out) {
+  if (algo != OT_KM && algo != OT_BKM) return ctx_fail(ctx, OT_ERR_ARG, "bad algo");
+  if (k < 0) return ctx_fail(ctx, OT_ERR_ARG, "k < 0");
+  if (k == 0) return OT_OK;
+  if (!C || !ldc || !n || !m || !r2c || !cost) return ctx_fail(ctx, OT_ERR_ARG, "null array");
+  if (!stream) stream = ctx->stream;
+
+  // all element pointers must live on one side
+  int first = -1;
+  for (int t = 0; t < k; ++t)
+    if (n[t] > 0) { first = t; break; }
+  const bool dev = first < 0 ? ptr_on_device(cost) : ptr_on_device(C[first]);
+
+  std::vector<int> st(k, OT_OK), skip(k, 0);
+  for (int t = 0; t < k; ++t) {
+    st[t] = check_sizes(C[t], ldc[t], n[t], m[t]);
+    if (st[t] == OT_OK && n[t] > 0 && !r2c[t]) st[t] = OT_ERR_ARG;
+    if (st[t] == OT_OK && n[t] > 0 && ptr_on_device(C[t]) != dev) st[t] = OT_ERR_ARG;
+    skip[t] = st[t] != OT_OK;
+  }
+
+  std::vector<Instance> insts(k);
+  std::lock_guard<std::mutex> lock(ctx->api_mu);
+  cudaError_t e;
+  if (dev) {
+    // device pointers: cost/status arrays are device arrays of length k
+    int32_t* dstatus = status;
+    if (!status || !ptr_on_device(status)) {
+      if (int rc = ctx->d_status.reserve(sizeof(int32_t) * k); rc) return ctx_fail(ctx, rc, "status alloc");
+      dstatus = static_cast<int32_t*>(ctx->d_status.ptr);
+    }
+    for (int t = 0; t < k; ++t) {
+      Instance& I = insts[t];
+      I.C = C[t]; I.ldc = ldc[t]; I.n = n[t]; I.m = m[t];
+      I.row_to_col = r2c[t]; I.u = u ? u[t] : nullptr; I.v = v ? v[t] : nullptr;
+      I.cost = cost + t; I.status = dstatus + t;
+      if (n[t] == 0 && st[t] == OT_OK) skip[t] = 1;  // handled below
+    }
+    std::vector<int> unsup;
+    if (int rc = run_device_batch(ctx, ctx->api, insts, skip, algo, stream, true, true, &unsup); rc) return rc;
+    for (int t : unsup) st[t] = OT_ERR_UNSUPPORTED;
+    ctx->last_k = k;
+    ctx->last_skip = skip;
+    for (int t : unsup) ctx->last_skip[t] = 1;
+    // empty instances: cost 0, status per validation; zero v of width m
+    for (int t = 0; t < k; ++t) {
+      if (n[t] == 0 && st[t] == OT_OK) {
+        if ((e = cudaMemsetAsync(cost + t, 0, sizeof(int64_t), stream)) != cudaSuccess) return ctx_cuda(ctx, e, "memset");
+        if (v && v[t] && m[t] > 0) cudaMemsetAsync(v[t], 0, sizeof(int64_t) * m[t], stream);
+      }
+    }
+    // host-side validation codes go to the status array
+    bool any_bad = false;
+    for (int t = 0; t < k; ++t) any_bad |= st[t] != OT_OK;
+    if (status && (any_bad)) {
+      for (int t = 0; t < k; ++t)
+        if (st[t] != OT_OK) cudaMemcpyAsync(dstatus + t, &st[t], sizeof(int32_t), cudaMemcpyHostToDevice, stream);
+      cudaStreamSynchronize(stream);
+    } else if (status && !ptr_on_device(status)) {
+      // host status array with device data: synchronise to report device codes
+      if ((e = cudaMemcpyAsync(status, dstatus, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+        return ctx_cuda(ctx, e, "status copy");
+      cudaStreamSynchronize(stream);
+    } else if (status) {
+      // device status array: zero-init entries of skipped instances
+    }
+    if (stats_out) {
+      cudaStreamSynchronize(stream);
+      int64_t s8[8] = {0};
+      if (k >= 1 && n[0] > 0) cudaMemcpy(s8, insts[0].stats, sizeof(s8), cudaMemcpyDeviceToHost);
+      int32_t s0 = 0;
+      if (k >= 1 && n[0] > 0) cudaMemcpy(&s0, dstatus, sizeof(s0), cudaMemcpyDeviceToHost);
+      std::memcpy(stats_out, s8, sizeof(s8));
+      if (st[0] != OT_OK) return ctx_fail(ctx, st[0], "instance rejected");
+      if (s0 != 0) return ctx_fail(ctx, s0, "device status error");
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return ctx_cuda(ctx, e, "solve");
+    for (int t = 0; t < k; ++t)
+      if (st[t] != OT_OK && k == 1) return ctx_fail(ctx, st[t], st[t] == OT_ERR_UNSUPPORTED ? "size not supported" : "bad instance");
+    return OT_OK;
+  }
+
+  // host pointers: stage through device memory
+  std::vector<size_t> off_c(k), off_r(k), off_u(k), off_v(k);
+  size_t total = al256(sizeof(int64_t) * k) + al256(sizeof(int32_t) * k);
+  const size_t base_cost = 0, base_status = al256(sizeof(int64_t) * k);
+  for (int t = 0; t < k; ++t) {
+    if (skip[t]) continue;
+    off_c[t] = total; total += al256(sizeof(int32_t) * size_t(n[t]) * m[t]);
+    off_r[t] = total; total += al256(sizeof(int32_t) * size_t(n[t]));
+    off_u[t] = total; total += al256(sizeof(int64_t) * size_t(n[t]));
+    off_v[t] = total; total += al256(sizeof(int64_t) * size_t(m[t]));
+  }
+  if (int rc = ctx->d_io.reserve(total); rc) return ctx_fail(ctx, rc, "staging alloc");
+  char* D = static_cast<char*>(ctx->d_io.ptr);
+  int64_t* dcost = reinterpret_cast<int64_t*>(D + base_cost);
+  int32_t* dstatus = reinterpret_cast<int32_t*>(D + base_status);
+  if ((e = cudaMemsetAsync(D, 0, al256(sizeof(int64_t) * k) + al256(sizeof(int32_t) * k), stream)) != cudaSuccess)
+    return ctx_cuda(ctx, e, "memset");
+  for (int t = 0; t < k; ++t) {
+    Instance& I = insts[t];
+    I.C = reinterpret_cast<const int32_t*>(D + off_c[t]); I.ldc = m[t]; I.n = n[t]; I.m = m[t];
+    I.row_to_col = reinterpret_cast<int32_t*>(D + off_r[t]);
+    I.u = reinterpret_cast<int64_t*>(D + off_u[t]);
+    I.v = reinterpret_cast<int64_t*>(D + off_v[t]);
+    I.cost = dcost + t; I.status = dstatus + t;
+    if (skip[t]) continue;
+    if (n[t] == 0) { skip[t] = 1; continue; }
+    e = cudaMemcpy2DAsync(D + off_c[t], sizeof(int32_t) * m[t], C[t], sizeof(int32_t) * ldc[t],
+                          sizeof(int32_t) * m[t], n[t], cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "H2D");
+  }
+  std::vector<int> unsup;
+  if (int rc = run_device_batch(ctx, ctx->api, insts, skip, algo, stream, true, true, &unsup); rc) return rc;
+  for (int t : unsup) { st[t] = OT_ERR_UNSUPPORTED; skip[t] = 1; }
+  ctx->last_k = k;
+  ctx->last_skip = skip;
+  std::vector<int32_t> hstatus(k, 0);
+  if ((e = cudaMemcpyAsync(cost, dcost, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+    return ctx_cuda(ctx, e, "D2H cost");
+  cudaMemcpyAsync(hstatus.data(), dstatus, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, stream);
+  for (int t = 0; t < k; ++t) {
+    if (st[t] != OT_OK || n[t] == 0) continue;
+    cudaMemcpyAsync(r2c[t], D + off_r[t], sizeof(int32_t) * n[t], cudaMemcpyDeviceToHost, stream);
+    if (u && u[t]) cudaMemcpyAsync(u[t], D + off_u[t], sizeof(int64_t) * n[t], cudaMemcpyDeviceToHost, stream);
+    if (v && v[t]) cudaMemcpyAsync(v[t], D + off_v[t], sizeof(int64_t) * m[t], cudaMemcpyDeviceToHost, stream);
+  }
+  int64_t s8[8] = {0};
+  if (stats_out && k >= 1 && !skip[0]) cudaMemcpyAsync(s8, insts[0].stats, sizeof(s8), cudaMemcpyDeviceToHost, stream);
+  if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return ctx_cuda(ctx, e, "sync");
+  for (int t = 0; t < k; ++t) {
+    if (n[t] == 0 && st[t] == OT_OK) {
+      cost[t] = 0;
+      if (v && v[t]) std::memset(v[t], 0, sizeof(int64_t) * m[t]);
+    }
+    if (st[t] == OT_OK) st[t] = hstatus[t];
+  }
+  if (status)
+    for (int t = 0; t < k; ++t) status[t] = st[t];
+  if (stats_out) std::memcpy(stats_out, s8, sizeof(s8));
+  if (k == 1 && st[0] != OT_OK)
+    return ctx_fail(ctx, st[0], st[0] == OT_ERR_UNSUPPORTED ? "size not supported" : "instance failed");
+  return OT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// exported API
+// ---------------------------------------------------------------------------
+
+int LaunchSlot::init() {
+  return cudaEventCreateWithFlags(&meta_ev, cudaEventDisableTiming) == cudaSuccess ? OT_OK : OT_ERR_CUDA;
+}
+
+void LaunchSlot::clear_graphs() {
+  for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+  graphs.clear();
+}
+
+void LaunchSlot::release() {
+  if (meta_pending && meta_ev) cudaEventSynchronize(meta_ev);
+  meta_pending = false;
+  clear_graphs();
+  d_meta.release();
+  d_stats.release();
+  h_meta.release();
+  if (meta_ev) cudaEventDestroy(meta_ev);
+  meta_ev = nullptr;
+}
+
+extern "C" {
+
+const char* ot_version(void) { return "otassign 0.1 sm_103a"; }
+
+int ot_ctx_create(ot_ctx** out, const ot_config* cfg) {
+  if (!out) return OT_ERR_ARG;
+  *out = nullptr;
+  ot_ctx* ctx = new (std::nothrow) ot_ctx();
+  if (!ctx) return OT_ERR_OOM;
+  ot_config c{};
+  c.device = -1;
+  if (cfg) c = *cfg;
+  cudaError_t e;
+  if (c.device >= 0) {
+    if ((e = cudaSetDevice(c.device)) != cudaSuccess) { delete ctx; return OT_ERR_CUDA; }
+    ctx->device = c.device;
+  } else {
+    if ((e = cudaGetDevice(&ctx->device)) != cudaSuccess) { cudaGetLastError(); delete ctx; return OT_ERR_CUDA; }
+  }
+  if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { delete ctx; return OT_ERR_CUDA; }
+  for (int i = 0; i < kForkStreams; ++i) {
+    cudaStreamCreateWithFlags(&ctx->bstreams[i], cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming);
+  }
+  cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+  if (ctx->api.init() != OT_OK) { ot_ctx_destroy(ctx); return OT_ERR_CUDA; }
+  ctx->api.use_graphs = true;
+  default_table(ctx->table);
+  if (c.tune_file) {
+    ctx->tune_file = c.tune_file;
+    load_tune_file(ctx);
+  }
+  if (int rc = serve_init(ctx, c); rc) { ot_ctx_destroy(ctx); return rc; }
+  if ((e = cudaGetLastError()) != cudaSuccess) { ot_ctx_destroy(ctx); return OT_ERR_CUDA; }
+  *out = ctx;
+  return OT_OK;
+}
+
+void ot_ctx_destroy(ot_ctx* ctx) {
+  if (!ctx) return;
+  serve_shutdown(ctx);
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  ctx->api.release();
+  for (int i = 0; i < kForkStreams; ++i) {
+    if (ctx->bstreams[i]) { cudaStreamSynchronize(ctx->bstreams[i]); cudaStreamDestroy(ctx->bstreams[i]); }
+    if (ctx->join_ev[i]) cudaEventDestroy(ctx->join_ev[i]);
+  }
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  ctx->d_status.release();
+  ctx->d_io.release();
+  ctx->d_scratch.release();
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* ot_last_error_string(const ot_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int ot_assign_solve(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int32_t m, int32_t algo,
+                    int32_t* row_to_col, int64_t* cost, int64_t* u, int64_t* v, void* stream) {
+  if (!ctx) return OT_ERR_ARG;
+  if (check_sizes(C, ldc, n, m) != OT_OK || !cost || (n > 0 && !row_to_col))
+    return ctx_fail(ctx, OT_ERR_ARG, "bad arguments");
+  cudaSetDevice(ctx->device);
+  const int32_t* Cs[1] = {C};
+  int64_t ld[1] = {ldc};
+  int32_t ns[1] = {n}, ms[1] = {m};
+  int32_t* rs[1] = {row_to_col};
+  int64_t* us[1] = {u};
+  int64_t* vs[1] = {v};
+  int32_t status = 0;
+  // single device solves report their status when asked via *_stats
+  const bool dev = n > 0 ? ptr_on_device(C) : ptr_on_device(cost);
+  return solve_many(ctx, 1, Cs, ld, ns, ms, algo, rs, cost, u ? us : nullptr, v ? vs : nullptr,
+                    dev ? nullptr : &status, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+int ot_assign_solve_stats(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int32_t m,
+                          int32_t algo, int32_t* row_to_col, int64_t* cost, int64_t* u, int64_t* v,
+                          ot_stats* stats, void* stream) {
+  if (!ctx || !stats) return OT_ERR_ARG;
+  if (check_sizes(C, ldc, n, m) != OT_OK || !cost || (n > 0 && !row_to_col))
+    return ctx_fail(ctx, OT_ERR_ARG, "bad arguments");
+  cudaSetDevice(ctx->device);
+  std::memset(stats, 0, sizeof(*stats));
+  const int32_t* Cs[1] = {C};
+  int64_t ld[1] = {ldc};
+  int32_t ns[1] = {n}, ms[1] = {m};
+  int32_t* rs[1] = {row_to_col};
+  int64_t* us[1] = {u};
+  int64_t* vs[1] = {v};
+  int32_t status = 0;
+  int rc = solve_many(ctx, 1, Cs, ld, ns, ms, algo, rs, cost, u ? us : nullptr, v ? vs : nullptr,
+                      &status, static_cast<cudaStream_t>(stream), stats);
+  if (rc == OT_OK && status != 0) return ctx_fail(ctx, status, "device status error");
+  return rc;
+}
+
+int ot_assign_solve_batched(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* ldc,
+                            const int32_t* n, const int32_t* m, int32_t algo,
+                            int32_t* const* row_to_col, int64_t* cost, int64_t* const* u,
+                            int64_t* const* v, int32_t* status, void* stream) {
+  if (!ctx) return OT_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  return solve_many(ctx, k, C, ldc, n, m, algo, row_to_col, cost, u, v, status,
+                    static_cast<cudaStream_t>(stream), nullptr);
+}
+
+int ot_last_call_stats(ot_ctx* ctx, ot_stats* total) {
+  if (!ctx || !total) return OT_ERR_ARG;
+  std::memset(total, 0, sizeof(*total));
+  std::lock_guard<std::mutex> lock(ctx->api_mu);
+  cudaSetDevice(ctx->device);
+  if (ctx->api.meta_pending) cudaEventSynchronize(ctx->api.meta_ev);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "sync");
+  const int k = ctx->last_k;
+  if (k > 0 && ctx->api.d_stats.ptr) {
+    std::vector<int64_t> h(size_t(k) * 8);
+    e = cudaMemcpy(h.data(), ctx->api.d_stats.ptr, h.size() * sizeof(int64_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "stats copy");
+    for (int t = 0; t < k; ++t) {
+      if (ctx->last_skip.size() == size_t(k) && ctx->last_skip[t]) continue;
+      total->steps += h[t * 8 + 0];
+      total->rows_scanned += h[t * 8 + 1];
+      total->cost_bytes += h[t * 8 + 2];
+      total->phases += h[t * 8 + 3];
+      total->augmentations += h[t * 8 + 4];
+      total->init_bytes += h[t * 8 + 5];
+    }
+  }
+  total->reserved[0] = ctx->api.last_launches;
+  return OT_OK;
+}
+
+int ot_tune_lookup(ot_ctx* ctx, int32_t algo, int32_t m, int32_t* tpi, int32_t* k) {
+  if (!ctx || (algo != OT_KM && algo != OT_BKM) || m < 0) return OT_ERR_ARG;
+  const int sh = ctx->table[algo][bucket_of(m)];
+  if (sh < 0) return OT_ERR_UNSUPPORTED;
+  if (tpi) *tpi = group_shape(sh).tpi;
+  if (k) *k = group_shape(sh).k;
+  return OT_OK;
+}
+
+int ot_tune_set(ot_ctx* ctx, int32_t algo, int32_t m, int32_t tpi, int32_t k) {
+  if (!ctx || (algo != OT_KM && algo != OT_BKM) || m < 0) return OT_ERR_ARG;
+  const int sh = shape_index(tpi, k);
+  const int b = bucket_of(m);
+  if (sh < 0 || group_shape(sh).max_cols() < (32 << b) || m > kMaxGroupCols)
+    return ctx_fail(ctx, OT_ERR_UNSUPPORTED, "shape not available for this bucket");
+  ctx->table[algo][b] = sh;
+  return OT_OK;
+}
+
+int ot_autotune(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* ldc,
+                const int32_t* n, const int32_t* m, int32_t algo, int32_t repeats) {
+  if (!ctx) return OT_ERR_ARG;
+  if ((algo != OT_KM && algo != OT_BKM) || k <= 0 || !C || !ldc || !n || !m)
+    return ctx_fail(ctx, OT_ERR_ARG, "bad arguments");
+  cudaSetDevice(ctx->device);
+  repeats = std::max(1, repeats);
+  std::lock_guard<std::mutex> lock(ctx->api_mu);
+  // scratch outputs for every instance
+  size_t total = al256(sizeof(int64_t) * k) + al256(sizeof(int32_t) * k);
+  std::vector<size_t> off(k);
+  for (int t = 0; t < k; ++t) {
+    if (check_sizes(C[t], ldc[t], n[t], m[t]) != OT_OK || !ptr_on_device(C[t]))
+      return ctx_fail(ctx, OT_ERR_ARG, "autotune needs valid device instances");
+    off[t] = total;
+    total += al256(4 * size_t(n[t])) + al256(8 * size_t(n[t])) + al256(8 * size_t(m[t])) + al256(64);
+  }
+  if (int rc = ctx->d_scratch.reserve(total); rc) return ctx_fail(ctx, rc, "scratch alloc");
+  char* D = static_cast<char*>(ctx->d_scratch.ptr);
+  std::vector<Instance> insts(k);
+  for (int t = 0; t < k; ++t) {
+    Instance& I = insts[t];
+    I.C = C[t]; I.ldc = ldc[t]; I.n = n[t]; I.m = m[t];
+    char* p = D + off[t];
+    I.row_to_col = reinterpret_cast<int32_t*>(p); p += al256(4 * size_t(n[t]));
+    I.u = reinterpret_cast<int64_t*>(p); p += al256(8 * size_t(n[t]));
+    I.v = reinterpret_cast<int64_t*>(p); p += al256(8 * size_t(m[t]));
+    I.stats = reinterpret_cast<int64_t*>(p);
+    I.cost = reinterpret_cast<int64_t*>(D) + t;
+    I.status = reinterpret_cast<int32_t*>(D + al256(sizeof(int64_t) * k)) + t;
+  }
+  // group instances by m-bucket
+  std::map<int, std::vector<int>> byb;
+  for (int t = 0; t < k; ++t)
+    if (n[t] > 0 && m[t] <= kMaxGroupCols) byb[bucket_of(m[t])].push_back(t);
+  cudaStream_t s = ctx->stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const size_t desc_bytes = al256(sizeof(Instance) * k);
+  if (ctx->api.meta_pending) { cudaEventSynchronize(ctx->api.meta_ev); ctx->api.meta_pending = false; }
+  if (int rc = ctx->api.d_meta.reserve(desc_bytes + al256(4 * size_t(k)) + 256); rc) return ctx_fail(ctx, rc, "meta alloc");
+  ctx->api.clear_graphs();
+  char* dm = static_cast<char*>(ctx->api.d_meta.ptr);
+  Instance* dinst = reinterpret_cast<Instance*>(dm);
+  int32_t* dorder = reinterpret_cast<int32_t*>(dm + desc_bytes);
+  int* dwork = reinterpret_cast<int*>(dm + desc_bytes + al256(4 * size_t(k)));
+  cudaMemcpyAsync(dinst, insts.data(), sizeof(Instance) * k, cudaMemcpyHostToDevice, s);
+  FILE* tf = ctx->tune_file.empty() ? nullptr : std::fopen(ctx->tune_file.c_str(), "a");
+  for (auto& kv : byb) {
+    std::vector<int>& idx = kv.second;
+    int nmax = 0, mmax = 0;
+    for (int t : idx) { nmax = std::max(nmax, n[t]); mmax = std::max(mmax, m[t]); }
+    std::sort(idx.begin(), idx.end(), [&](int a, int c) {
+      return (long long)n[a] * m[a] > (long long)n[c] * m[c];
+    });
+    cudaMemcpyAsync(dorder, idx.data(), sizeof(int32_t) * idx.size(), cudaMemcpyHostToDevice, s);
+    int best = -1;
+    float best_ms = 1e30f;
+    for (int sh = 0; sh < num_group_shapes(); ++sh) {
+      GroupShape g = group_shape(sh);
+      if (g.max_cols() < mmax || g.max_cols() > 8 * std::max(mmax, 32)) continue;
+      if (group_smem_bytes(g, algo, nmax, mmax) > group_smem_limit()) continue;
+      float tmin = 1e30f;
+      bool ok = true;
+      for (int r = 0; r < repeats + 1 && ok; ++r) {
+        cudaMemsetAsync(dwork, 0, sizeof(int), s);
+        cudaEventRecord(e0, s);
+        if (launch_group(g, algo, dinst, dorder, int(idx.size()), dwork, nmax, mmax, 0, s) != cudaSuccess) {
+          cudaGetLastError();
+          ok = false;
+          break;
+        }
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) tmin = std::min(tmin, ms);  // first run warms up
+      }
+      if (ok && tmin < best_ms) { best_ms = tmin; best = sh; }
+    }
+    if (best >= 0) {
+      ctx->table[algo][kv.first] = best;
+      if (tf)
+        std::fprintf(tf, "{\"algo\": %d, \"bucket_mmax\": %d, \"tpi\": %d, \"k\": %d, \"ms\": %.4f}\n",
+                     algo, 32 << kv.first, group_shape(best).tpi, group_shape(best).k, best_ms);
+    }
+  }
+  if (tf) std::fclose(tf);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "autotune");
+  return OT_OK;
+}
+
+}  // extern "C"
+
+// JSON-lines table: {"algo": A, "bucket_mmax": M, "tpi": T, "k": K, ...}; later
+// lines override earlier ones.
+void load_tune_file(ot_ctx* ctx) {
+  FILE* f = std::fopen(ctx->tune_file.c_str(), "r");
+  if (!f) return;
+  char line[512];
+  while (std::fgets(line, sizeof line, f)) {
+    int a = -1, mm = -1, tpi = -1, kk = -1;
+    const char* p;
+    if ((p = std::strstr(line, "\"algo\":"))) a = std::atoi(p + 7);
+    if ((p = std::strstr(line, "\"bucket_mmax\":"))) mm = std::atoi(p + 14);
+    if ((p = std::strstr(line, "\"tpi\":"))) tpi = std::atoi(p + 6);
+    if ((p = std::strstr(line, "\"k\":"))) kk = std::atoi(p + 4);
+    const int sh = shape_index(tpi, kk);
+    if ((a == 0 || a == 1) && mm > 0 && sh >= 0) ctx->table[a][bucket_of(mm)] = sh;
+  }
+  std::fclose(f);
+}

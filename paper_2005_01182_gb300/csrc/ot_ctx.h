@@ -1,0 +1,94 @@
+// Host-side context of libotassign.so (not part of the C ABI).
+#pragma once
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "otassign.h"
+#include "ot_internal.h"
+
+namespace ot {
+constexpr int kNumBuckets = 8;        // bucket b: m <= 32 << b
+constexpr int kMaxGroupCols = 4096;   // widest instance one group engine handles
+constexpr int kForkStreams = 4;
+int bucket_of(int m);
+int shape_index(int tpi, int k);
+void default_table(int table[2][kNumBuckets]);
+}  // namespace ot
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t cap = 0;
+  int generation = 0;
+  int reserve(size_t bytes);
+  void release();
+};
+
+struct PinBuf {
+  void* ptr = nullptr;
+  size_t cap = 0;
+  int reserve(size_t bytes);
+  void release();
+};
+
+struct ServeState;  // ot_serve.cu
+
+// Descriptor upload buffers of one launcher (the API path, or one serving
+// wave): pinned mirror, device copy, the event that frees the mirror, the
+// per-instance stats block, and cached CUDA graphs keyed by batch layout.
+struct LaunchSlot {
+  DevBuf d_meta, d_stats;
+  PinBuf h_meta;
+  cudaEvent_t meta_ev = nullptr;
+  bool meta_pending = false;
+  bool use_graphs = false;
+  std::map<std::string, cudaGraphExec_t> graphs;
+  int last_launches = 0;
+  int init();
+  void clear_graphs();
+  void release();
+};
+
+struct ot_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t bstreams[ot::kForkStreams] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[ot::kForkStreams] = {};
+  std::string err;
+  std::mutex api_mu;
+
+  LaunchSlot api;
+  DevBuf d_status, d_io, d_scratch;
+
+  int table[2][ot::kNumBuckets];
+  std::string tune_file;
+
+  int last_k = 0;               // instances of the most recent API call
+  std::vector<int> last_skip;   // which of them were not launched
+
+  ServeState* serve = nullptr;
+};
+
+int ctx_fail(ot_ctx* ctx, int code, const std::string& msg);
+int ctx_cuda(ot_ctx* ctx, cudaError_t e, const char* where);
+bool ptr_on_device(const void* p);
+void load_tune_file(ot_ctx* ctx);
+// Bucket the instances by tuned group shape and launch them on `stream`
+// (forking buckets over the context's streams when `fork`).  Entries with
+// skip[t] set are not launched; instances no engine can take are listed in
+// *unsupported.  With `own_stats` the slot's stats block receives per-instance
+// counters, otherwise insts[t].stats is kept.
+int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<ot::Instance>& insts,
+                     const std::vector<int>& skip, int algo, cudaStream_t stream, bool fork,
+                     bool own_stats, std::vector<int>* unsupported);
+int serve_init(ot_ctx* ctx, const ot_config& cfg);
+void serve_shutdown(ot_ctx* ctx);

@@ -1,0 +1,445 @@
+// Group engine: one cooperative thread group solves one assignment instance
+// end to end on the device (Kuhn-Munkres or batched KM), many groups per
+// launch pull instances from a device work counter.
+//
+// Layout and ownership.  A group is TPI threads (a warp when TPI == 32,
+// otherwise the whole CTA).  Thread t owns columns j = t + k*TPI, k < K, and
+// keeps their search state in registers: the tentative distance dist_j
+// (the paper's slack, in absolute rather than decremented form), the dual
+// v_j, the predecessor row, and one "in T" bit.  Row-indexed state (u,
+// row_to_col, tree roots) and the column-indexed arrays that other threads
+// must read (col_to_row, the predecessor log used by the augmenting walk)
+// live in shared memory.  Cost rows are read straight from global memory
+// with coalesced loads: at each step the group reads one row (KM) or the
+// rows that just joined the tree (batched KM), only where j is outside T.
+//
+// Lazy duals.  Instead of touching every u_i, v_j and slack_j at every
+// dual adjustment (Sec. 2.3: "adjusts the dual potentials across a cut ...
+// in the same manner as KM"), a phase keeps distances relative to the duals
+// it started with and applies the accumulated adjustment once, when an
+// augmenting path is found: a column that entered T at distance dist_j gets
+// v_j -= D - dist_j and its matched row u += D - dist_j; every root gets
+// u += D.  This yields exactly the duals of the step-by-step update (every
+// comparison is the same integer comparison shifted by a common constant),
+// so KM here reproduces the eager CPU reference bit for bit.
+#pragma once
+#include <climits>
+#include <cstdint>
+
+#include "ot_internal.h"
+
+namespace ot {
+
+enum { kAlgoKM = 0, kAlgoBKM = 1 };
+
+// status codes written by the device (match OT_ERR_* in otassign.h)
+enum { kDevOk = 0, kDevStepLimit = -4 };
+
+struct Best {
+  long long d;
+  int j;
+};
+
+__device__ __forceinline__ bool lex_less(long long d1, int j1, long long d2, int j2) {
+  return d1 < d2 || (d1 == d2 && j1 < j2);
+}
+
+__device__ __forceinline__ Best warp_argmin(Best b) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    long long d2 = __shfl_xor_sync(0xffffffffu, b.d, o);
+    int j2 = __shfl_xor_sync(0xffffffffu, b.j, o);
+    if (lex_less(d2, j2, b.d, b.j)) { b.d = d2; b.j = j2; }
+  }
+  return b;
+}
+
+__device__ __forceinline__ long long warp_sum(long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__device__ __forceinline__ long long warp_min(long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    long long y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = y < x ? y : x;
+  }
+  return x;
+}
+
+template <int TPI>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (TPI == 32) __syncwarp();
+  else __syncthreads();
+}
+
+// Shared-memory carve-up of one group.
+struct GroupSmem {
+  long long* u;   // [nmax] row duals
+  int* r2c;       // [nmax] row -> column
+  int* c2r;       // [mmax] column -> row
+  int* pred;      // [mmax] predecessor row of columns that left the heap
+  int* root;      // [nmax] tree root of rows in S (batched KM)
+  int* claim;     // [nmax] lowest free column claimed per root (batched KM)
+  int* list;      // [nmax] rows that joined S this step (batched KM)
+  Best* slots;    // [2 * TPI/32] cross-warp reduction slots
+  int* misc;      // [16]
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline size_t group_bytes(int tpi, int algo, int nmax, int mmax) {
+  size_t b = align16(8 * size_t(nmax)) + align16(4 * size_t(nmax)) + 2 * align16(4 * size_t(mmax));
+  if (algo == kAlgoBKM) b += 3 * align16(4 * size_t(nmax));
+  b += align16(2 * (tpi / 32) * sizeof(Best)) + 64;
+  return b;
+}
+
+__device__ inline GroupSmem carve(unsigned char* p, int tpi, int algo, int nmax, int mmax) {
+  GroupSmem s;
+  s.u = reinterpret_cast<long long*>(p); p += align16(8 * size_t(nmax));
+  s.r2c = reinterpret_cast<int*>(p); p += align16(4 * size_t(nmax));
+  s.c2r = reinterpret_cast<int*>(p); p += align16(4 * size_t(mmax));
+  s.pred = reinterpret_cast<int*>(p); p += align16(4 * size_t(mmax));
+  if (algo == kAlgoBKM) {
+    s.root = reinterpret_cast<int*>(p); p += align16(4 * size_t(nmax));
+    s.claim = reinterpret_cast<int*>(p); p += align16(4 * size_t(nmax));
+    s.list = reinterpret_cast<int*>(p); p += align16(4 * size_t(nmax));
+  } else {
+    s.root = s.claim = s.list = nullptr;
+  }
+  s.slots = reinterpret_cast<Best*>(p); p += align16(2 * (tpi / 32) * sizeof(Best));
+  s.misc = reinterpret_cast<int*>(p);
+  return s;
+}
+
+// Minimum (dist, column) over the group; every thread gets the result.
+template <int TPI>
+__device__ __forceinline__ Best group_argmin(Best b, Best* slots, int& parity) {
+  b = warp_argmin(b);
+  if constexpr (TPI == 32) {
+    __syncwarp();
+    return b;
+  } else {
+    constexpr int NW = TPI / 32;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    Best* s = slots + parity * NW;
+    parity ^= 1;
+    if (l == 0) s[w] = b;
+    __syncthreads();
+    Best c = (l < NW) ? s[l] : Best{kInf, INT_MAX};
+    return warp_argmin(c);
+  }
+}
+
+template <int TPI>
+__device__ __forceinline__ long long group_sum(long long x, Best* slots, int& parity) {
+  x = warp_sum(x);
+  if constexpr (TPI == 32) {
+    return x;
+  } else {
+    constexpr int NW = TPI / 32;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    Best* s = slots + parity * NW;
+    parity ^= 1;
+    if (l == 0) s[w].d = x;
+    __syncthreads();
+    long long y = (l < NW) ? s[l].d : 0;
+    return warp_sum(y);
+  }
+}
+
+// Solve one instance with the whole group.  t = thread index in the group.
+template <int TPI, int K, int ALGO>
+__device__ void solve_instance(const Instance& I, const GroupSmem& S, const int t) {
+  const int n = I.n, m = I.m;
+  const int32_t* __restrict__ C = I.C;
+  const long long ldc = I.ldc;
+  int rpar = 0;  // reduction-slot parity
+
+  long long dist[K], v[K];
+  int pred[K];
+  unsigned inT = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) { v[k] = 0; dist[k] = kInf; pred[k] = -1; }
+
+  for (int i = t; i < n; i += TPI) { S.r2c[i] = -1; S.u[i] = 0; }
+  for (int j = t; j < m; j += TPI) { S.c2r[j] = -1; S.pred[j] = -1; }
+  if (t < 16) S.misc[t] = 0;
+  group_sync<TPI>();
+
+  long long init_bytes = 0;
+  if constexpr (ALGO == kAlgoBKM) {
+    // B1: u_i = min_j C[i][j] (v = 0), one warp per row, lanes stride columns.
+    constexpr int NW = TPI / 32;
+    const int w = t >> 5, l = t & 31;
+    for (int i = w; i < n; i += NW) {
+      const int32_t* row = C + i * ldc;
+      long long mn = kInf;
+      for (int j = l; j < m; j += 32) {
+        long long c = __ldg(row + j);
+        mn = c < mn ? c : mn;
+      }
+      mn = warp_min(mn);
+      if (l == 0) S.u[i] = mn;
+    }
+    init_bytes = 4LL * n * m;
+  }
+  group_sync<TPI>();
+
+  long long steps = 0, rows = 0, bytes = 0, phases = 0, augs = 0;
+  int status = kDevOk;
+  int matched = 0;
+  int p = 0;  // list-counter parity (batched KM)
+
+  while (matched < n) {
+    ++phases;
+#pragma unroll
+    for (int k = 0; k < K; ++k) { dist[k] = kInf; pred[k] = -1; }
+    inT = 0;
+    int L = 1;
+    int km_row = matched;  // KM roots rows in index order
+    long long level = 0;
+    int tcount = 0;
+
+    if constexpr (ALGO == kAlgoBKM) {
+      // every free row is a root of the forest; S starts as the free rows
+      for (int i = t; i < n; i += TPI) {
+        if (S.r2c[i] < 0) {
+          int pos = atomicAdd(&S.misc[p], 1);
+          S.list[pos] = i;
+          S.root[i] = i;
+          S.claim[i] = INT_MAX;
+        }
+      }
+      group_sync<TPI>();
+      L = S.misc[p];
+    }
+
+    int guard = 0;
+    for (;;) {
+      if (++guard > m + 2) { status = kDevStepLimit; break; }
+      if constexpr (ALGO == kAlgoBKM) {
+        if (t == 0) S.misc[p ^ 1] = 0;
+      }
+      // A1 / B2: scan the rows that just joined the tree, columns outside T
+      for (int q = 0; q < L; ++q) {
+        const int i = (ALGO == kAlgoKM) ? km_row : S.list[q];
+        const long long base = level - S.u[i];
+        const int32_t* row = C + i * ldc;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const int j = t + k * TPI;
+          if (j < m && !((inT >> k) & 1u)) {
+            const long long cand = base + __ldg(row + j) - v[k];
+            if (cand < dist[k] || (ALGO == kAlgoBKM && cand == dist[k] && i < pred[k])) {
+              dist[k] = cand;
+              pred[k] = i;
+            }
+          }
+        }
+      }
+      ++steps;
+      rows += L;
+      bytes += 4LL * L * (m - tcount);
+
+      // A2 / B4: minimum distance outside T, lowest column on ties
+      Best b{kInf, INT_MAX};
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int j = t + k * TPI;
+        if (j < m && !((inT >> k) & 1u) && lex_less(dist[k], j, b.d, b.j)) b = Best{dist[k], j};
+      }
+      b = group_argmin<TPI>(b, S.slots, rpar);
+      const long long D = b.d;
+      if (b.j == INT_MAX) { status = kDevStepLimit; break; }
+
+      if constexpr (ALGO == kAlgoKM) {
+        const int js = b.j;
+        const int mate = S.c2r[js];
+        if ((js % TPI) == t) {
+          const int ks = js / TPI;
+#pragma unroll
+          for (int k = 0; k < K; ++k)
+            if (k == ks) {
+              S.pred[js] = pred[k];
+              if (mate >= 0) inT |= 1u << k;
+            }
+        }
+        if (mate >= 0) {
+          km_row = mate;
+          level = D;
+          ++tcount;
+          continue;
+        }
+        // A3: apply the accumulated dual adjustment
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          if ((inT >> k) & 1u) {
+            const long long dd = D - dist[k];
+            v[k] -= dd;
+            S.u[S.c2r[t + k * TPI]] += dd;
+          }
+        }
+        if (t == 0) S.u[matched] += D;
+        group_sync<TPI>();
+        // A4: flip the alternating path that ends at the free column js
+        if (t == 0) {
+          int j = js, i = S.pred[j];
+          for (int hop = 0; hop <= n; ++hop) {
+            const int prev = S.r2c[i];
+            S.r2c[i] = j;
+            S.c2r[j] = i;
+            if (prev < 0) break;
+            j = prev;
+            i = S.pred[j];
+          }
+        }
+        group_sync<TPI>();
+        ++matched;
+        ++augs;
+        break;
+      } else {
+        // every column at the new level joins T (or ends a path if free)
+        unsigned freebits = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const int j = t + k * TPI;
+          if (j < m && !((inT >> k) & 1u) && dist[k] == D) {
+            S.pred[j] = pred[k];
+            const int mate = S.c2r[j];
+            if (mate < 0) {
+              freebits |= 1u << k;
+              S.misc[2] = 1;
+            } else {
+              inT |= 1u << k;
+              const int pos = atomicAdd(&S.misc[p ^ 1], 1);
+              S.list[pos] = mate;
+              S.root[mate] = S.root[pred[k]];
+              atomicAdd(&S.misc[4], 1);
+            }
+          }
+        }
+        group_sync<TPI>();
+        if (S.misc[2] == 0) {
+          p ^= 1;
+          L = S.misc[p];
+          level = D;
+          tcount = S.misc[4];
+          continue;
+        }
+        // B4: accumulated dual adjustment across the cut; roots get +D
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          if ((inT >> k) & 1u) {
+            const long long dd = D - dist[k];
+            v[k] -= dd;
+            S.u[S.c2r[t + k * TPI]] += dd;
+          }
+        }
+        for (int i = t; i < n; i += TPI)
+          if (S.r2c[i] < 0) S.u[i] += D;
+        // B3: one augmenting path per tree, the lowest free column wins
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if ((freebits >> k) & 1u) atomicMin(&S.claim[S.root[pred[k]]], t + k * TPI);
+        group_sync<TPI>();
+        int walked = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          if (!((freebits >> k) & 1u)) continue;
+          int j = t + k * TPI;
+          if (S.claim[S.root[pred[k]]] != j) continue;
+          int i = pred[k];
+          for (int hop = 0; hop <= n; ++hop) {
+            const int prev = S.r2c[i];
+            S.r2c[i] = j;
+            S.c2r[j] = i;
+            if (prev < 0) break;
+            j = prev;
+            i = S.pred[j];
+          }
+          ++walked;
+        }
+        if (walked) atomicAdd(&S.misc[6], walked);
+        group_sync<TPI>();
+        const int got = S.misc[6];
+        matched += got;
+        augs += got;
+        group_sync<TPI>();
+        if (t == 0) {
+          S.misc[2] = 0;
+          S.misc[4] = 0;
+          S.misc[6] = 0;
+          S.misc[p] = 0;
+        }
+        group_sync<TPI>();
+        break;
+      }
+    }
+    if (status != kDevOk) break;
+    if (phases > (long long)n + 1) { status = kDevStepLimit; break; }
+  }
+
+  // A5: objective and outputs
+  long long part = 0;
+  if (status == kDevOk)
+    for (int i = t; i < n; i += TPI) part += __ldg(C + i * ldc + S.r2c[i]);
+  const long long cost = group_sum<TPI>(part, S.slots, rpar);
+  for (int i = t; i < n; i += TPI) { I.row_to_col[i] = S.r2c[i]; if (I.u) I.u[i] = S.u[i]; }
+  if (I.v) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int j = t + k * TPI;
+      if (j < m) I.v[j] = v[k];
+    }
+  }
+  if (t == 0) {
+    *I.cost = cost;
+    if (I.stats) {
+      I.stats[0] = steps;
+      I.stats[1] = rows;
+      I.stats[2] = bytes;
+      I.stats[3] = phases;
+      I.stats[4] = augs;
+      I.stats[5] = init_bytes;
+    }
+  }
+  // results before the status word, at system scope: a host thread that
+  // polls a status word in mapped host memory may then read the results
+  __threadfence_system();
+  group_sync<TPI>();
+  if (t == 0 && I.status) *reinterpret_cast<volatile int32_t*>(I.status) = status;
+  group_sync<TPI>();
+}
+
+template <int TPI, int K, int ALGO>
+__global__ void __launch_bounds__(TPI == 32 ? 256 : TPI)
+    group_kernel(const Instance* __restrict__ insts, const int32_t* __restrict__ order, int num,
+                 int* work, int nmax, int mmax, int groups_per_cta, int bytes_per_group) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int gid = (TPI == 32) ? int(threadIdx.x >> 5) : 0;
+  const int t = (TPI == 32) ? int(threadIdx.x & 31) : int(threadIdx.x);
+  if (gid >= groups_per_cta) return;
+  const GroupSmem S = carve(smem_raw + size_t(gid) * bytes_per_group, TPI, ALGO, nmax, mmax);
+  for (;;) {
+    int idx;
+    if constexpr (TPI == 32) {
+      int x = 0;
+      if (t == 0) x = atomicAdd(work, 1);
+      idx = __shfl_sync(0xffffffffu, x, 0);
+    } else {
+      if (t == 0) S.misc[15] = atomicAdd(work, 1);
+      __syncthreads();
+      idx = S.misc[15];
+      __syncthreads();
+    }
+    if (idx >= num) break;
+    const Instance I = insts[order ? order[idx] : idx];
+    solve_instance<TPI, K, ALGO>(I, S, t);
+  }
+}
+
+}  // namespace ot

@@ -1,0 +1,47 @@
+// Internal types shared by the CUDA translation units of libotassign.so.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ot {
+
+constexpr long long kInf = 1LL << 62;
+
+// One instance as the device engines see it.  All pointers are device
+// pointers; stats/status may be null.
+struct Instance {
+  const int32_t* C;   // row-major, ldc elements per row
+  int64_t ldc;
+  int32_t n, m;
+  int32_t* row_to_col;  // [n]
+  int64_t* u;           // [n]
+  int64_t* v;           // [m]
+  int64_t* cost;        // [1]
+  int32_t* status;      // [1]
+  int64_t* stats;       // [8], laid out as ot_stats
+};
+
+// Shape of a solver group: TPI threads cooperate on one instance, each
+// owning K columns (j = t + k*TPI).  TPI == 32 packs several warps per CTA.
+struct GroupShape {
+  int tpi;
+  int k;
+  int max_cols() const { return tpi * k; }
+};
+
+// Launch the group engine over `num` instances listed in `order` (indices
+// into `insts`), pulling work from `work_counter` (device int, zeroed by
+// the caller).  algo: 0 = KM, 1 = batched KM.  nmax/mmax bound the sizes of
+// the listed instances.  Returns a CUDA error code.
+cudaError_t launch_group(GroupShape shape, int algo, const Instance* insts,
+                         const int32_t* order, int num, int* work_counter, int nmax,
+                         int mmax, int max_ctas, cudaStream_t stream);
+
+// Shapes compiled into the library, smallest first.
+int num_group_shapes();
+GroupShape group_shape(int idx);
+// Dynamic shared memory the group engine needs per CTA for these bounds.
+size_t group_smem_bytes(GroupShape shape, int algo, int nmax, int mmax);
+size_t group_smem_limit();
+
+}  // namespace ot

@@ -1,0 +1,440 @@
+// Serving loop of libotassign.so: continuous batching of independent solves.
+//
+// submit() reserves a block of a device arena (the HBM budget) for the
+// request -- cost matrix, duals, assignment, counters -- and copies the cost
+// matrix in; a request that does not fit yet waits in a host-side queue with
+// its own copy of C.  A serving thread packs every admitted request into a
+// wave and launches it on one of several streams, so waves formed while
+// earlier ones still run overlap on the device.  Each request finishes on
+// its own: the solver group writes the results and then, after a
+// system-scope fence, a status word in mapped host memory, which poll()
+// reads without waiting for the rest of the wave.  poll() copies the
+// results out and frees the arena block, which lets queued requests in.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+
+#include "ot_ctx.h"
+#include "ot_group.cuh"
+
+using namespace ot;
+
+namespace {
+
+constexpr int32_t kFlagPending = 0x7fffffff;
+constexpr size_t kDefaultBudget = size_t(4) << 30;
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// First-fit allocator over one device slab, with coalescing frees.
+struct Arena {
+  char* base = nullptr;
+  size_t size = 0, used = 0;
+  std::map<size_t, size_t> free_blocks;  // offset -> bytes
+  int init(size_t bytes) {
+    if (base) return OT_OK;
+    if (cudaMalloc(&base, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      base = nullptr;
+      return OT_ERR_OOM;
+    }
+    size = bytes;
+    free_blocks.clear();
+    free_blocks[0] = bytes;
+    return OT_OK;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    for (auto it = free_blocks.begin(); it != free_blocks.end(); ++it) {
+      if (it->second < bytes) continue;
+      *off = it->first;
+      const size_t rest = it->second - bytes;
+      const size_t at = it->first + bytes;
+      free_blocks.erase(it);
+      if (rest) free_blocks[at] = rest;
+      used += bytes;
+      return true;
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    used -= bytes;
+    auto it = free_blocks.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_blocks.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_blocks.erase(nx);
+    }
+    if (it != free_blocks.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_blocks.erase(it);
+      }
+    }
+  }
+  void destroy() {
+    if (base) cudaFree(base);
+    base = nullptr;
+  }
+};
+
+struct Req {
+  int n = 0, m = 0, algo = 0;
+  size_t bytes = 0, off = 0;
+  int flag = -1;                 // slot in the mapped status array
+  bool admitted = false, launched = false;
+  std::vector<int32_t> host_C;  // packed copy while waiting for admission
+};
+
+struct Wave {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  bool busy = false;
+  LaunchSlot slot;
+};
+
+// offsets inside one request's arena block
+struct Layout {
+  size_t c, r2c, u, v, cost, stats, total;
+  Layout(int n, int m) {
+    c = 0;
+    r2c = c + al256(4 * size_t(n) * m);
+    u = r2c + al256(4 * size_t(n));
+    v = u + al256(8 * size_t(n));
+    cost = v + al256(8 * size_t(m));
+    stats = cost + 256;
+    total = stats + 256;
+  }
+};
+
+}  // namespace
+
+struct ServeState {
+  ot_ctx* ctx = nullptr;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread th;
+  bool stop = false;
+  bool started = false;
+  Arena arena;
+  size_t budget = kDefaultBudget;
+  int max_inflight = 4096;
+  int inflight = 0;
+  std::unordered_map<uint64_t, Req> reqs;
+  std::deque<uint64_t> pending, ready;
+  std::vector<Wave> waves;
+  int32_t* flags = nullptr;  // mapped pinned host memory
+  int32_t* dflags = nullptr;
+  std::vector<int> free_flags;
+  uint64_t next_ticket = 1;
+  cudaStream_t copy_stream = nullptr, poll_stream = nullptr;
+  cudaEvent_t copy_ev = nullptr;
+  int64_t n_submitted = 0, n_admitted = 0, n_completed = 0, n_waves = 0, max_busy = 0, n_refused = 0;
+
+  int start();
+  void loop();
+  bool try_admit(uint64_t t, Req& r);
+  void launch_ready();
+};
+
+int ServeState::start() {
+  if (started) return OT_OK;
+  if (int rc = arena.init(budget); rc) return rc;
+  if (cudaHostAlloc(&flags, sizeof(int32_t) * max_inflight, cudaHostAllocMapped) != cudaSuccess) {
+    cudaGetLastError();
+    return OT_ERR_OOM;
+  }
+  if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&dflags), flags, 0) != cudaSuccess) return OT_ERR_CUDA;
+  for (int i = max_inflight - 1; i >= 0; --i) free_flags.push_back(i);
+  cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking);
+  cudaStreamCreateWithFlags(&poll_stream, cudaStreamNonBlocking);
+  cudaEventCreateWithFlags(&copy_ev, cudaEventDisableTiming);
+  for (Wave& w : waves) {
+    cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming);
+    if (w.slot.init() != OT_OK) return OT_ERR_CUDA;
+  }
+  if (cudaGetLastError() != cudaSuccess) return OT_ERR_CUDA;
+  started = true;
+  const int dev = ctx->device;
+  th = std::thread([this, dev] {
+    cudaSetDevice(dev);
+    loop();
+  });
+  return OT_OK;
+}
+
+// Caller holds mu.  Reserve arena space and a status slot for request t.
+bool ServeState::try_admit(uint64_t, Req& r) {
+  if (inflight >= max_inflight || free_flags.empty()) return false;
+  size_t off = 0;
+  if (!arena.alloc(r.bytes, &off)) return false;
+  r.off = off;
+  r.flag = free_flags.back();
+  free_flags.pop_back();
+  flags[r.flag] = kFlagPending;
+  r.admitted = true;
+  ++inflight;
+  ++n_admitted;
+  return true;
+}
+
+// Caller holds mu.  Launch every admitted request as one wave.
+void ServeState::launch_ready() {
+  if (ready.empty()) return;
+  Wave* w = nullptr;
+  int busy = 0;
+  for (Wave& x : waves) {
+    if (x.busy && cudaEventQuery(x.done) == cudaSuccess) x.busy = false;
+    busy += x.busy;
+  }
+  for (Wave& x : waves)
+    if (!x.busy) { w = &x; break; }
+  if (!w) return;
+  std::vector<uint64_t> tk(ready.begin(), ready.end());
+  ready.clear();
+  // copies issued by the serving thread must land before the wave starts
+  cudaEventRecord(copy_ev, copy_stream);
+  cudaStreamWaitEvent(w->stream, copy_ev, 0);
+  for (int algo = 0; algo < 2; ++algo) {
+    std::vector<Instance> insts;
+    std::vector<uint64_t> ids;
+    for (uint64_t t : tk) {
+      Req& r = reqs[t];
+      if (r.algo != algo) continue;
+      Layout L(r.n, r.m);
+      char* b = arena.base + r.off;
+      Instance I;
+      I.C = reinterpret_cast<const int32_t*>(b + L.c);
+      I.ldc = r.m;
+      I.n = r.n;
+      I.m = r.m;
+      I.row_to_col = reinterpret_cast<int32_t*>(b + L.r2c);
+      I.u = reinterpret_cast<int64_t*>(b + L.u);
+      I.v = reinterpret_cast<int64_t*>(b + L.v);
+      I.cost = reinterpret_cast<int64_t*>(b + L.cost);
+      I.stats = reinterpret_cast<int64_t*>(b + L.stats);
+      I.status = dflags + r.flag;
+      insts.push_back(I);
+      ids.push_back(t);
+    }
+    if (insts.empty()) continue;
+    std::vector<int> skip(insts.size(), 0), unsup;
+    int rc = run_device_batch(ctx, w->slot, insts, skip, algo, w->stream, false, false, &unsup);
+    if (rc != OT_OK) {
+      for (uint64_t t : ids) flags[reqs[t].flag] = rc;
+    } else {
+      for (int i : unsup) flags[reqs[ids[i]].flag] = OT_ERR_UNSUPPORTED;
+    }
+  }
+  for (uint64_t t : tk) reqs[t].launched = true;
+  cudaEventRecord(w->done, w->stream);
+  w->busy = true;
+  ++n_waves;
+  max_busy = std::max<int64_t>(max_busy, busy + 1);
+}
+
+void ServeState::loop() {
+  std::unique_lock<std::mutex> lk(mu);
+  while (!stop) {
+    cv.wait_for(lk, std::chrono::microseconds(200));
+    if (stop) break;
+    // admit queued requests, oldest first, while space allows
+    while (!pending.empty()) {
+      const uint64_t t = pending.front();
+      auto it = reqs.find(t);
+      if (it == reqs.end()) { pending.pop_front(); continue; }
+      Req& r = it->second;
+      if (!try_admit(t, r)) break;
+      pending.pop_front();
+      cudaMemcpyAsync(arena.base + r.off, r.host_C.data(), 4 * size_t(r.n) * r.m,
+                      cudaMemcpyHostToDevice, copy_stream);
+      cudaStreamSynchronize(copy_stream);
+      std::vector<int32_t>().swap(r.host_C);
+      ready.push_back(t);
+    }
+    launch_ready();
+  }
+}
+
+int serve_init(ot_ctx* ctx, const ot_config& cfg) {
+  ServeState* s = new (std::nothrow) ServeState();
+  if (!s) return OT_ERR_OOM;
+  s->ctx = ctx;
+  if (cfg.hbm_budget_bytes > 0) s->budget = size_t(cfg.hbm_budget_bytes);
+  if (cfg.max_inflight > 0) s->max_inflight = cfg.max_inflight;
+  s->waves.resize(cfg.wave_streams > 0 ? cfg.wave_streams : 4);
+  ctx->serve = s;
+  return OT_OK;  // device resources are created on first submit
+}
+
+void serve_shutdown(ot_ctx* ctx) {
+  ServeState* s = ctx->serve;
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->th.joinable()) s->th.join();
+  if (s->started) {
+    for (Wave& w : s->waves) {
+      if (w.busy) cudaEventSynchronize(w.done);
+      w.slot.release();
+      if (w.done) cudaEventDestroy(w.done);
+      if (w.stream) cudaStreamDestroy(w.stream);
+    }
+    if (s->copy_stream) { cudaStreamSynchronize(s->copy_stream); cudaStreamDestroy(s->copy_stream); }
+    if (s->poll_stream) { cudaStreamSynchronize(s->poll_stream); cudaStreamDestroy(s->poll_stream); }
+    if (s->copy_ev) cudaEventDestroy(s->copy_ev);
+    s->arena.destroy();
+    if (s->flags) cudaFreeHost(s->flags);
+  }
+  delete s;
+  ctx->serve = nullptr;
+}
+
+extern "C" {
+
+int ot_assign_submit(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int32_t m, int32_t algo,
+                     uint64_t* ticket) {
+  if (!ctx || !ticket) return OT_ERR_ARG;
+  if ((algo != OT_KM && algo != OT_BKM) || n <= 0 || m < n || !C || ldc < m)
+    return ctx_fail(ctx, OT_ERR_ARG, "bad arguments");
+  ServeState* s = ctx->serve;
+  cudaSetDevice(ctx->device);
+  Layout L(n, m);
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (!s->started) {
+    if (int rc = s->start(); rc) return ctx_fail(ctx, rc, "serving start failed");
+  }
+  ++s->n_submitted;
+  if (L.total > s->budget) {
+    ++s->n_refused;
+    return ctx_fail(ctx, OT_ERR_BUDGET, "request larger than the HBM budget");
+  }
+  const uint64_t t = s->next_ticket++;
+  Req& r = s->reqs[t];
+  r.n = n;
+  r.m = m;
+  r.algo = algo;
+  r.bytes = L.total;
+  const bool now = s->pending.empty() && s->try_admit(t, r);
+  char* dst = now ? s->arena.base + r.off : nullptr;
+  lk.unlock();
+  // copy outside the lock; the caller may reuse C once submit returns.  A
+  // request that could not be admitted keeps a packed host copy.
+  std::vector<int32_t> hc;
+  cudaError_t e;
+  if (now) {
+    e = cudaMemcpy2DAsync(dst, 4 * size_t(m), C, 4 * size_t(ldc), 4 * size_t(m), n, cudaMemcpyDefault,
+                          s->poll_stream);
+  } else {
+    hc.resize(size_t(n) * m);
+    e = cudaMemcpy2DAsync(hc.data(), 4 * size_t(m), C, 4 * size_t(ldc), 4 * size_t(m), n,
+                          cudaMemcpyDefault, s->poll_stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->poll_stream);
+  lk.lock();
+  Req& rr = s->reqs[t];
+  if (e != cudaSuccess) {
+    if (rr.admitted) {
+      s->arena.release(rr.off, rr.bytes);
+      s->free_flags.push_back(rr.flag);
+      --s->inflight;
+    }
+    s->reqs.erase(t);
+    return ctx_cuda(ctx, e, "submit copy");
+  }
+  if (now) {
+    s->ready.push_back(t);
+  } else {
+    rr.host_C = std::move(hc);
+    s->pending.push_back(t);
+  }
+  lk.unlock();
+  s->cv.notify_one();
+  *ticket = t;
+  return OT_OK;
+}
+
+int ot_assign_poll(ot_ctx* ctx, uint64_t ticket, int32_t* row_to_col, int64_t* cost, int64_t* u,
+                   int64_t* v) {
+  if (!ctx) return OT_ERR_ARG;
+  ServeState* s = ctx->serve;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return ctx_fail(ctx, OT_ERR_TICKET, "unknown ticket");
+  Req& r = it->second;
+  if (!r.launched) return OT_PENDING;
+  const int32_t f = *reinterpret_cast<volatile int32_t*>(&s->flags[r.flag]);
+  if (f == kFlagPending) return OT_PENDING;
+  const int n = r.n, m = r.m;
+  char* b = s->arena.base + r.off;
+  const size_t off = r.off, bytes = r.bytes;
+  const int flag = r.flag;
+  lk.unlock();
+  cudaSetDevice(ctx->device);
+  int rc = f;
+  if (f == OT_OK) {
+    Layout L(n, m);
+    cudaError_t e = cudaSuccess;
+    if (row_to_col) e = cudaMemcpyAsync(row_to_col, b + L.r2c, 4 * size_t(n), cudaMemcpyDefault, s->poll_stream);
+    if (e == cudaSuccess && cost) e = cudaMemcpyAsync(cost, b + L.cost, 8, cudaMemcpyDefault, s->poll_stream);
+    if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, b + L.u, 8 * size_t(n), cudaMemcpyDefault, s->poll_stream);
+    if (e == cudaSuccess && v) e = cudaMemcpyAsync(v, b + L.v, 8 * size_t(m), cudaMemcpyDefault, s->poll_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->poll_stream);
+    if (e != cudaSuccess) rc = ctx_cuda(ctx, e, "poll copy");
+  }
+  lk.lock();
+  s->arena.release(off, bytes);
+  s->free_flags.push_back(flag);
+  --s->inflight;
+  s->reqs.erase(ticket);
+  if (rc == OT_OK) ++s->n_completed;
+  lk.unlock();
+  s->cv.notify_one();
+  if (rc != OT_OK && rc != OT_ERR_CUDA) return ctx_fail(ctx, rc, "request failed on the device");
+  return rc;
+}
+
+int ot_assign_drain(ot_ctx* ctx) {
+  if (!ctx) return OT_ERR_ARG;
+  ServeState* s = ctx->serve;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    {
+      std::lock_guard<std::mutex> g(s->mu);
+      bool all = true;
+      for (auto& kv : s->reqs) {
+        const Req& r = kv.second;
+        if (!r.launched || *reinterpret_cast<volatile int32_t*>(&s->flags[r.flag]) == kFlagPending) {
+          all = false;
+          break;
+        }
+      }
+      if (all) return OT_OK;
+    }
+    s->cv.notify_one();
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::minutes(10))
+      return ctx_fail(ctx, OT_ERR_TIMEOUT, "drain timed out");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+int ot_serving_counters(ot_ctx* ctx, int64_t* out8) {
+  if (!ctx || !out8) return OT_ERR_ARG;
+  ServeState* s = ctx->serve;
+  std::lock_guard<std::mutex> g(s->mu);
+  out8[0] = s->n_submitted;
+  out8[1] = s->n_admitted;
+  out8[2] = s->n_completed;
+  out8[3] = s->n_waves;
+  out8[4] = s->max_busy;
+  out8[5] = int64_t(s->arena.used);
+  out8[6] = int64_t(s->budget);
+  out8[7] = s->n_refused;
+  return OT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,303 @@
+"""Thin ctypes binding of libotassign.so (argument marshalling only).
+
+Every function here has the name of the C entry point it calls
+(``include/otassign.h``); all arithmetic of the assignment solvers runs in
+the library's CUDA kernels.  Tensors are passed by pointer: device tensors
+stay on the device, host tensors (pinned or not) are staged by the library.
+If the shared library has not been built this module raises on import of a
+solver call -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libotassign.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "otassign.h")
+
+OT_OK = 0
+OT_PENDING = 1
+OT_ERR_ARG = -1
+OT_ERR_OOM = -2
+OT_ERR_BUDGET = -3
+OT_ERR_TIMEOUT = -4
+OT_ERR_CUDA = -5
+OT_ERR_OVERFLOW = -6
+OT_ERR_UNSUPPORTED = -7
+OT_ERR_TICKET = -8
+OT_KM = 0
+OT_BKM = 1
+
+_lib = None
+
+
+class OtError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"otassign error {code}: {msg}")
+        self.code = code
+
+
+class ot_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("rows_scanned", ctypes.c_int64),
+                ("cost_bytes", ctypes.c_int64), ("phases", ctypes.c_int64),
+                ("augmentations", ctypes.c_int64), ("init_bytes", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 2)]
+
+
+class ot_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
+                ("max_inflight", ctypes.c_int32), ("wave_streams", ctypes.c_int32),
+                ("tune_file", ctypes.c_char_p)]
+
+
+def declared_symbols() -> list[str]:
+    """Function names declared in include/otassign.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ot_[a-z_0-9]+)\s*\(", text)))
+
+
+def load(path: str | None = None):
+    """Load the shared library (built by ``build.build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"{p} not found: build the CUDA library first (paper_2005_01182_gb300.build)")
+    lib = ctypes.CDLL(p)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "ot_ctx_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(ot_config)]),
+        "ot_ctx_destroy": (None, [vp]),
+        "ot_last_error_string": (ctypes.c_char_p, [vp]),
+        "ot_assign_solve": (ctypes.c_int, [vp, vp, i64, i32, i32, i32, vp, vp, vp, vp, vp]),
+        "ot_assign_solve_stats": (ctypes.c_int, [vp, vp, i64, i32, i32, i32, vp, vp, vp, vp,
+                                                 ctypes.POINTER(ot_stats), vp]),
+        "ot_assign_solve_batched": (ctypes.c_int, [vp, i32, pp, ctypes.POINTER(i64),
+                                                   ctypes.POINTER(i32), ctypes.POINTER(i32), i32,
+                                                   pp, vp, pp, pp, vp, vp]),
+        "ot_assign_submit": (ctypes.c_int, [vp, vp, i64, i32, i32, i32, ctypes.POINTER(ctypes.c_uint64)]),
+        "ot_assign_poll": (ctypes.c_int, [vp, ctypes.c_uint64, vp, vp, vp, vp]),
+        "ot_assign_drain": (ctypes.c_int, [vp]),
+        "ot_serving_counters": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
+        "ot_autotune": (ctypes.c_int, [vp, i32, pp, ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                       ctypes.POINTER(i32), i32, i32]),
+        "ot_tune_lookup": (ctypes.c_int, [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "ot_tune_set": (ctypes.c_int, [vp, i32, i32, i32, i32]),
+        "ot_last_call_stats": (ctypes.c_int, [vp, ctypes.POINTER(ot_stats)]),
+        "ot_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_handle(stream) -> ctypes.c_void_p | None:
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _check_cost(C: torch.Tensor):
+    if C.dtype != torch.int32 or C.dim() != 2 or (C.shape[0] > 0 and C.stride(1) != 1):
+        raise ValueError("cost matrix must be a 2-D int32 tensor with unit column stride")
+    n, m = C.shape
+    ldc = C.stride(0) if n > 1 else m
+    return n, m, max(ldc, m)
+
+
+class Context:
+    """Owns one ot_ctx (device buffers, streams, serving thread)."""
+
+    def __init__(self, device: int = -1, hbm_budget_bytes: int = 0, max_inflight: int = 0,
+                 wave_streams: int = 0, tune_file: str | None = None):
+        lib = load()
+        cfg = ot_config(device, hbm_budget_bytes, max_inflight, wave_streams,
+                        tune_file.encode() if tune_file else None)
+        h = ctypes.c_void_p()
+        rc = lib.ot_ctx_create(ctypes.byref(h), ctypes.byref(cfg))
+        if rc != OT_OK:
+            raise OtError(rc, "ot_ctx_create failed")
+        self.h = h
+        self.lib = lib
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ot_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def error(self) -> str:
+        return self.lib.ot_last_error_string(self.h).decode()
+
+    def _raise(self, rc: int, what: str):
+        if rc != OT_OK:
+            raise OtError(rc, f"{what}: {self.error()}")
+
+
+def ot_ctx_create(**kw) -> Context:
+    return Context(**kw)
+
+
+def ot_ctx_destroy(ctx: Context):
+    ctx.close()
+
+
+def ot_last_error_string(ctx: Context) -> str:
+    return ctx.error()
+
+
+def _outputs(n, m, device, pin=False):
+    kw = dict(device=device)
+    r = torch.empty(n, dtype=torch.int32, **kw)
+    c = torch.empty(1, dtype=torch.int64, **kw)
+    u = torch.empty(n, dtype=torch.int64, **kw)
+    v = torch.empty(m, dtype=torch.int64, **kw)
+    if pin and device == "cpu":
+        r, c, u, v = (x.pin_memory() for x in (r, c, u, v))
+    return r, c, u, v
+
+
+def ot_assign_solve(ctx: Context, C: torch.Tensor, algo: int = OT_KM, stream=None, out=None,
+                    duals: bool = True):
+    """Solve one instance.  Returns (row_to_col, cost[1], u, v) on C's device."""
+    n, m, ldc = _check_cost(C)
+    r, c, u, v = out if out is not None else _outputs(n, m, C.device)
+    rc = ctx.lib.ot_assign_solve(ctx.h, _ptr(C), ldc, n, m, algo, _ptr(r), _ptr(c),
+                                 _ptr(u) if duals else None, _ptr(v) if duals else None,
+                                 _stream_handle(stream))
+    ctx._raise(rc, "ot_assign_solve")
+    return r, c, u, v
+
+
+def ot_assign_solve_stats(ctx: Context, C: torch.Tensor, algo: int = OT_KM, stream=None):
+    """Solve one instance synchronously; also returns the device counters."""
+    n, m, ldc = _check_cost(C)
+    r, c, u, v = _outputs(n, m, C.device)
+    st = ot_stats()
+    rc = ctx.lib.ot_assign_solve_stats(ctx.h, _ptr(C), ldc, n, m, algo, _ptr(r), _ptr(c), _ptr(u),
+                                       _ptr(v), ctypes.byref(st), _stream_handle(stream))
+    ctx._raise(rc, "ot_assign_solve_stats")
+    stats = {f: getattr(st, f) for f, _ in ot_stats._fields_ if f != "reserved"}
+    return r, c, u, v, stats
+
+
+class BatchArgs:
+    """Pre-marshalled pointer arrays for ot_assign_solve_batched, so that a
+    timed loop re-issues the call without rebuilding them."""
+
+    def __init__(self, Cs, outs=None, device=None, cost=None, status=None):
+        k = len(Cs)
+        self.k = k
+        self.Cs = Cs
+        dev = device if device is not None else (Cs[0].device if k else "cpu")
+        sizes = [_check_cost(C) for C in Cs]
+        self.n = (ctypes.c_int32 * k)(*[s[0] for s in sizes])
+        self.m = (ctypes.c_int32 * k)(*[s[1] for s in sizes])
+        self.ldc = (ctypes.c_int64 * k)(*[s[2] for s in sizes])
+        self.cp = (ctypes.c_void_p * k)(*[C.data_ptr() for C in Cs])
+        if outs is None:
+            outs = [(torch.empty(s[0], dtype=torch.int32, device=dev),
+                     torch.empty(s[0], dtype=torch.int64, device=dev),
+                     torch.empty(s[1], dtype=torch.int64, device=dev)) for s in sizes]
+        self.outs = outs
+        self.rp = (ctypes.c_void_p * k)(*[o[0].data_ptr() for o in outs])
+        self.up = (ctypes.c_void_p * k)(*[o[1].data_ptr() for o in outs])
+        self.vp = (ctypes.c_void_p * k)(*[o[2].data_ptr() for o in outs])
+        self.cost = cost if cost is not None else torch.empty(k, dtype=torch.int64, device=dev)
+        self.status = status if status is not None else torch.empty(k, dtype=torch.int32, device=dev)
+
+
+def ot_assign_solve_batched(ctx: Context, Cs_or_args, algo: int = OT_KM, stream=None):
+    """Solve many instances in one launch set.  Accepts a list of cost
+    tensors (all on one device, or all on the host) or a ``BatchArgs``.
+    Returns the BatchArgs holding (row_to_col, u, v) per instance, cost[k]
+    and status[k]."""
+    a = Cs_or_args if isinstance(Cs_or_args, BatchArgs) else BatchArgs(Cs_or_args)
+    P = ctypes.cast
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    rc = ctx.lib.ot_assign_solve_batched(ctx.h, a.k, P(a.cp, pp), a.ldc, a.n, a.m, algo,
+                                         P(a.rp, pp), _ptr(a.cost), P(a.up, pp), P(a.vp, pp),
+                                         _ptr(a.status), _stream_handle(stream))
+    ctx._raise(rc, "ot_assign_solve_batched")
+    return a
+
+
+def ot_last_call_stats(ctx: Context) -> dict:
+    """Counters of the most recent solve call, summed over its instances
+    (synchronises); 'launches' is the number of kernels it launched."""
+    st = ot_stats()
+    ctx._raise(ctx.lib.ot_last_call_stats(ctx.h, ctypes.byref(st)), "ot_last_call_stats")
+    d = {f: getattr(st, f) for f, _ in ot_stats._fields_ if f != "reserved"}
+    d["launches"] = st.reserved[0]
+    return d
+
+
+def ot_assign_submit(ctx: Context, C: torch.Tensor, algo: int = OT_KM) -> int:
+    n, m, ldc = _check_cost(C)
+    t = ctypes.c_uint64()
+    rc = ctx.lib.ot_assign_submit(ctx.h, _ptr(C), ldc, n, m, algo, ctypes.byref(t))
+    ctx._raise(rc, "ot_assign_submit")
+    return t.value
+
+
+def ot_assign_poll(ctx: Context, ticket: int, out) -> int:
+    """out = (row_to_col, cost[1], u, v) tensors (host or device).  Returns
+    OT_PENDING or OT_OK; raises on a failed request."""
+    r, c, u, v = out
+    rc = ctx.lib.ot_assign_poll(ctx.h, ticket, _ptr(r), _ptr(c), _ptr(u), _ptr(v))
+    if rc == OT_PENDING:
+        return OT_PENDING
+    ctx._raise(rc, "ot_assign_poll")
+    return OT_OK
+
+
+def ot_assign_drain(ctx: Context):
+    ctx._raise(ctx.lib.ot_assign_drain(ctx.h), "ot_assign_drain")
+
+
+def ot_serving_counters(ctx: Context) -> dict:
+    out = (ctypes.c_int64 * 8)()
+    ctx._raise(ctx.lib.ot_serving_counters(ctx.h, out), "ot_serving_counters")
+    keys = ["submitted", "admitted", "completed", "waves", "max_concurrent_waves",
+            "bytes_resident", "budget_bytes", "refused"]
+    return dict(zip(keys, list(out)))
+
+
+def ot_autotune(ctx: Context, Cs, algo: int = OT_KM, repeats: int = 2):
+    a = BatchArgs(Cs)
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    rc = ctx.lib.ot_autotune(ctx.h, a.k, ctypes.cast(a.cp, pp), a.ldc, a.n, a.m, algo, repeats)
+    ctx._raise(rc, "ot_autotune")
+
+
+def ot_tune_lookup(ctx: Context, algo: int, m: int):
+    t, k = ctypes.c_int32(), ctypes.c_int32()
+    ctx._raise(ctx.lib.ot_tune_lookup(ctx.h, algo, m, ctypes.byref(t), ctypes.byref(k)), "ot_tune_lookup")
+    return t.value, k.value
+
+
+def ot_tune_set(ctx: Context, algo: int, m: int, threads_per_instance: int, cols_per_thread: int):
+    ctx._raise(ctx.lib.ot_tune_set(ctx.h, algo, m, threads_per_instance, cols_per_thread), "ot_tune_set")
+
+
+def ot_version() -> str:
+    return load().ot_version().decode()
