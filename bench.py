@@ -142,13 +142,15 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--k", type=int, default=4096)
     ap.add_argument("--sample", type=int, default=96)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--skip-extras", action="store_true")
+    ap.add_argument("--profile-once", action="store_true",
+                    help="untimed: 2 warm-up batched KM launches then 1 more, for an ncu capture")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -177,6 +179,14 @@ def main():
 
     Cs = batch_for_rank(rank, args.k)
     dC = [torch.from_numpy(C).to(dev) for C in Cs]
+    if args.profile_once:
+        a = ot.BatchArgs(dC)
+        for _ in range(3):
+            ot.ot_assign_solve_batched(ctx, a, ot.OT_KM, stream)
+        torch.cuda.synchronize()
+        assert (a.status.cpu().numpy() == 0).all()
+        ctx.close()
+        return
     h2d_bytes = sum(C.nbytes for C in Cs)
     d2h_bytes = sum(C.shape[0] * 4 + C.shape[0] * 8 + C.shape[1] * 8 + 8 for C in Cs)
     torch.cuda.synchronize()
@@ -234,14 +244,26 @@ def main():
     assert (args_dev.status.cpu().numpy() == 0).all(), "device status error"
 
     # ---- e2e through the C-ABI with pinned host buffers ---------------------
-    hC = [torch.from_numpy(C).pin_memory() for C in Cs]
-    houts = [(torch.empty(C.shape[0], dtype=torch.int32).pin_memory(),
-              torch.empty(C.shape[0], dtype=torch.int64).pin_memory(),
-              torch.empty(C.shape[1], dtype=torch.int64).pin_memory()) for C in Cs]
+    # one pinned slab per array kind, instances back to back
+    ns = [C.shape[0] for C in Cs]
+    ms = [C.shape[1] for C in Cs]
+    slabC = torch.empty(sum(n * m for n, m in zip(ns, ms)), dtype=torch.int32).pin_memory()
+    slabR = torch.empty(sum(ns), dtype=torch.int32).pin_memory()
+    slabU = torch.empty(sum(ns), dtype=torch.int64).pin_memory()
+    slabV = torch.empty(sum(ms), dtype=torch.int64).pin_memory()
+    hC, houts, oc, orow, ocol = [], [], 0, 0, 0
+    for C, n, m in zip(Cs, ns, ms):
+        v = slabC[oc:oc + n * m].view(n, m)
+        v.copy_(torch.from_numpy(C))
+        hC.append(v)
+        houts.append((slabR[orow:orow + n], slabU[orow:orow + n], slabV[ocol:ocol + m]))
+        oc += n * m
+        orow += n
+        ocol += m
     args_host = ot.BatchArgs(hC, outs=houts, device="cpu",
                              cost=torch.empty(args.k, dtype=torch.int64).pin_memory(),
                              status=torch.empty(args.k, dtype=torch.int32).pin_memory())
-    e2e_steps = max(3, args.steps // 2)
+    e2e_steps = max(3, min(20, args.steps // 2))
     ot.ot_assign_solve_batched(ctx, args_host, algo)
     barrier()
     w0 = time.perf_counter()

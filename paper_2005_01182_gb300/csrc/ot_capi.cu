@@ -387,34 +387,61 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
     return OT_OK;
   }
 
-  // host pointers: stage through device memory
+  // host pointers: stage through device memory.  Matrices, assignments and
+  // duals are packed back to back in staging (one region each), so that host
+  // buffers laid out the same way move with a single copy per region.
   std::vector<size_t> off_c(k), off_r(k), off_u(k), off_v(k);
-  size_t total = al256(sizeof(int64_t) * k) + al256(sizeof(int32_t) * k);
-  const size_t base_cost = 0, base_status = al256(sizeof(int64_t) * k);
+  size_t ec = 0, er = 0, ev = 0;  // element offsets
   for (int t = 0; t < k; ++t) {
+    off_c[t] = ec; off_r[t] = er; off_u[t] = er; off_v[t] = ev;
     if (skip[t]) continue;
-    off_c[t] = total; total += al256(sizeof(int32_t) * size_t(n[t]) * m[t]);
-    off_r[t] = total; total += al256(sizeof(int32_t) * size_t(n[t]));
-    off_u[t] = total; total += al256(sizeof(int64_t) * size_t(n[t]));
-    off_v[t] = total; total += al256(sizeof(int64_t) * size_t(m[t]));
+    ec += size_t(n[t]) * m[t];
+    er += size_t(n[t]);
+    ev += size_t(m[t]);
   }
+  const size_t base_cost = 0, base_status = al256(sizeof(int64_t) * k);
+  const size_t base_c = base_status + al256(sizeof(int32_t) * k);
+  const size_t base_r = base_c + al256(4 * ec), base_u = base_r + al256(4 * er);
+  const size_t base_v = base_u + al256(8 * er), total = base_v + al256(8 * ev);
   if (int rc = ctx->d_io.reserve(total); rc) return ctx_fail(ctx, rc, "staging alloc");
   char* D = static_cast<char*>(ctx->d_io.ptr);
   int64_t* dcost = reinterpret_cast<int64_t*>(D + base_cost);
   int32_t* dstatus = reinterpret_cast<int32_t*>(D + base_status);
-  if ((e = cudaMemsetAsync(D, 0, al256(sizeof(int64_t) * k) + al256(sizeof(int32_t) * k), stream)) != cudaSuccess)
-    return ctx_cuda(ctx, e, "memset");
+  int32_t* dC = reinterpret_cast<int32_t*>(D + base_c);
+  int32_t* dR = reinterpret_cast<int32_t*>(D + base_r);
+  int64_t* dU = reinterpret_cast<int64_t*>(D + base_u);
+  int64_t* dV = reinterpret_cast<int64_t*>(D + base_v);
+  if ((e = cudaMemsetAsync(D, 0, base_c, stream)) != cudaSuccess) return ctx_cuda(ctx, e, "memset");
+  // contiguity of the caller's host buffers
+  bool c_flat = true, r_flat = true, u_flat = u != nullptr, v_flat = v != nullptr;
+  int first_live = -1;
+  for (int t = 0; t < k; ++t) {
+    if (skip[t] || n[t] == 0) continue;
+    if (first_live < 0) first_live = t;
+    const int f = first_live;
+    c_flat &= ldc[t] == m[t] && C[t] == C[f] + off_c[t] - off_c[f];
+    r_flat &= r2c[t] == r2c[f] + off_r[t] - off_r[f];
+    if (u_flat) u_flat &= u[t] && u[t] == u[f] + off_u[t] - off_u[f];
+    if (v_flat) v_flat &= v[t] && v[t] == v[f] + off_v[t] - off_v[f];
+  }
   for (int t = 0; t < k; ++t) {
     Instance& I = insts[t];
-    I.C = reinterpret_cast<const int32_t*>(D + off_c[t]); I.ldc = m[t]; I.n = n[t]; I.m = m[t];
-    I.row_to_col = reinterpret_cast<int32_t*>(D + off_r[t]);
-    I.u = reinterpret_cast<int64_t*>(D + off_u[t]);
-    I.v = reinterpret_cast<int64_t*>(D + off_v[t]);
+    I.C = dC + off_c[t]; I.ldc = m[t]; I.n = n[t]; I.m = m[t];
+    I.row_to_col = dR + off_r[t];
+    I.u = dU + off_u[t];
+    I.v = dV + off_v[t];
     I.cost = dcost + t; I.status = dstatus + t;
     if (skip[t]) continue;
     if (n[t] == 0) { skip[t] = 1; continue; }
-    e = cudaMemcpy2DAsync(D + off_c[t], sizeof(int32_t) * m[t], C[t], sizeof(int32_t) * ldc[t],
-                          sizeof(int32_t) * m[t], n[t], cudaMemcpyHostToDevice, stream);
+    if (!c_flat) {
+      e = cudaMemcpy2DAsync(dC + off_c[t], sizeof(int32_t) * m[t], C[t], sizeof(int32_t) * ldc[t],
+                            sizeof(int32_t) * m[t], n[t], cudaMemcpyHostToDevice, stream);
+      if (e != cudaSuccess) return ctx_cuda(ctx, e, "H2D");
+    }
+  }
+  if (c_flat && first_live >= 0 && ec > 0) {
+    e = cudaMemcpyAsync(dC + off_c[first_live], C[first_live], 4 * (ec - off_c[first_live]),
+                        cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return ctx_cuda(ctx, e, "H2D");
   }
   std::vector<int> unsup;
@@ -426,11 +453,21 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
   if ((e = cudaMemcpyAsync(cost, dcost, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
     return ctx_cuda(ctx, e, "D2H cost");
   cudaMemcpyAsync(hstatus.data(), dstatus, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, stream);
+  const bool all_live = unsup.empty();
+  if (first_live >= 0 && all_live && r_flat)
+    cudaMemcpyAsync(r2c[first_live], dR + off_r[first_live], 4 * (er - off_r[first_live]), cudaMemcpyDeviceToHost, stream);
+  if (first_live >= 0 && all_live && u_flat)
+    cudaMemcpyAsync(u[first_live], dU + off_u[first_live], 8 * (er - off_u[first_live]), cudaMemcpyDeviceToHost, stream);
+  if (first_live >= 0 && all_live && v_flat)
+    cudaMemcpyAsync(v[first_live], dV + off_v[first_live], 8 * (ev - off_v[first_live]), cudaMemcpyDeviceToHost, stream);
   for (int t = 0; t < k; ++t) {
     if (st[t] != OT_OK || n[t] == 0) continue;
-    cudaMemcpyAsync(r2c[t], D + off_r[t], sizeof(int32_t) * n[t], cudaMemcpyDeviceToHost, stream);
-    if (u && u[t]) cudaMemcpyAsync(u[t], D + off_u[t], sizeof(int64_t) * n[t], cudaMemcpyDeviceToHost, stream);
-    if (v && v[t]) cudaMemcpyAsync(v[t], D + off_v[t], sizeof(int64_t) * m[t], cudaMemcpyDeviceToHost, stream);
+    if (!(all_live && r_flat))
+      cudaMemcpyAsync(r2c[t], dR + off_r[t], 4 * size_t(n[t]), cudaMemcpyDeviceToHost, stream);
+    if (u && u[t] && !(all_live && u_flat))
+      cudaMemcpyAsync(u[t], dU + off_u[t], 8 * size_t(n[t]), cudaMemcpyDeviceToHost, stream);
+    if (v && v[t] && !(all_live && v_flat))
+      cudaMemcpyAsync(v[t], dV + off_v[t], 8 * size_t(m[t]), cudaMemcpyDeviceToHost, stream);
   }
   int64_t s8[8] = {0};
   if (stats_out && k >= 1 && !skip[0]) cudaMemcpyAsync(s8, insts[0].stats, sizeof(s8), cudaMemcpyDeviceToHost, stream);
