@@ -167,6 +167,36 @@ int ot_tune_lookup(ot_ctx* ctx, int32_t algo, int32_t m, int32_t* threads_per_in
 int ot_tune_set(ot_ctx* ctx, int32_t algo, int32_t m, int32_t threads_per_instance,
                 int32_t cols_per_thread);
 
+/* Batched solve that allocates nothing on the device.  There is no
+ * counterpart in the paper: this is a packaging of ot_assign_solve_batched
+ * for callers that cannot call cudaMalloc -- for example code that runs
+ * while another component owns the whole device memory budget (an inference
+ * server's fixed arena, a framework allocator that must see every byte), or
+ * code on a path where an allocation's implicit synchronisation or failure
+ * is not acceptable.  It needs no context.
+ *
+ * The launch metadata (descriptors, launch order, work counters) goes to one
+ * static device array of fixed size that the library's module carries, held
+ * by every GPU that loads the library until the process exits.  Hence:
+ *   - at most OT_NOALLOC_MAX_INSTANCES instances per call (else
+ *     OT_ERR_UNSUPPORTED), each with m <= 4096 (else OT_ERR_UNSUPPORTED);
+ *   - every pointer (element pointers, cost[k], status[k] when given) must be
+ *     device memory on the current device (else OT_ERR_ARG): host data would
+ *     need staging memory;
+ *   - all calls share the array, so calls whose work overlaps on the GPU
+ *     (different streams or threads) race: serialise them;
+ *   - the first call on a device looks up the array's device address and may
+ *     load the module; make that first call before any stream capture.
+ * Results are identical to ot_assign_solve_batched's.  Asynchronous on
+ * `stream` (NULL = the legacy default stream); per-instance device status
+ * codes go to status[k] when it is non-NULL. */
+#define OT_NOALLOC_MAX_INSTANCES 1024
+int ot_assign_solve_batched_noalloc(int32_t k, const int32_t* const* C, const int64_t* ldc,
+                                    const int32_t* n, const int32_t* m, int32_t algo,
+                                    int32_t* const* row_to_col, int64_t* cost,
+                                    int64_t* const* u, int64_t* const* v, int32_t* status,
+                                    void* stream);
+
 /* Library version string, e.g. "otassign 0.1 sm_103a". */
 const char* ot_version(void);
 

@@ -1,0 +1,130 @@
+// ot_assign_solve_batched_noalloc: the multi-instance group engine launched
+// without any device allocation.
+//
+// The batched entry point normally stages its launch metadata (one
+// descriptor per instance, the per-bucket launch order and the work
+// counters the persistent groups pull instances from) in buffers that the
+// context allocates with cudaMalloc.  Here that scratch lives in one
+// file-scope __device__ array of fixed size, so a caller that must not
+// allocate device memory can still run batched solves.  The array is part
+// of the loaded module: every GPU that loads the library holds it until the
+// process exits.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "otassign.h"
+#include "ot_ctx.h"
+#include "ot_group.cuh"
+#include "ot_shapes.h"
+
+using namespace ot;
+
+namespace {
+
+constexpr int kNoAllocMaxInstances = OT_NOALLOC_MAX_INSTANCES;
+constexpr int kNoAllocMaxBuckets = 32;
+
+struct NoAllocScratch {
+  Instance desc[kNoAllocMaxInstances];
+  int32_t order[kNoAllocMaxInstances];
+  int32_t status[kNoAllocMaxInstances];
+  int32_t work[kNoAllocMaxBuckets];
+};
+
+// The shared scratch (about 82 KB: 72-byte descriptors, two int32 arrays).  Every call overwrites it; calls whose
+// work overlaps on the GPU race on it.
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+NoAllocScratch* g_scratch_addr[kMaxDevices] = {};
+
+// Once per device, with that device current: the device address of the
+// scratch array (its host-side name is only a stand-in, not an address a
+// kernel may use).
+int scratch_address(int dev, NoAllocScratch** out) {
+  if (dev < 0 || dev >= kMaxDevices) return OT_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> g(g_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return OT_ERR_CUDA;
+    g_scratch_addr[dev] = static_cast<NoAllocScratch*>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return OT_OK;
+}
+
+}  // namespace
+
+extern "C" int ot_assign_solve_batched_noalloc(int32_t k, const int32_t* const* C, const int64_t* ldc,
+                                               const int32_t* n, const int32_t* m, int32_t algo,
+                                               int32_t* const* row_to_col, int64_t* cost,
+                                               int64_t* const* u, int64_t* const* v, int32_t* status,
+                                               void* stream) {
+  if (algo != OT_KM && algo != OT_BKM) return OT_ERR_ARG;
+  if (k < 0 || (k > 0 && (!C || !ldc || !n || !m || !row_to_col || !cost))) return OT_ERR_ARG;
+  if (k > kNoAllocMaxInstances) return OT_ERR_UNSUPPORTED;  // beyond the static scratch
+  if (k == 0) return OT_OK;
+  if (!ptr_on_device(cost) || (status && !ptr_on_device(status))) return OT_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return OT_ERR_CUDA;
+  NoAllocScratch* S = nullptr;
+  if (int rc = scratch_address(dev, &S); rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  // Host-side bookkeeping on the stack (about 80 KB): descriptors and the
+  // bucket of each instance.
+  Instance hdesc[kNoAllocMaxInstances];
+  int32_t horder[kNoAllocMaxInstances];
+  int32_t hbucket[kNoAllocMaxInstances];
+  int table[2][kNumBuckets];
+  default_table(table);
+  int count[OT_NUM_GROUP_SHAPES] = {0}, nmax[OT_NUM_GROUP_SHAPES] = {0},
+      mmax[OT_NUM_GROUP_SHAPES] = {0};
+  for (int t = 0; t < k; ++t) {
+    if (n[t] < 1 || m[t] < n[t] || ldc[t] < m[t] || !C[t] || !row_to_col[t]) return OT_ERR_ARG;
+    if (m[t] > kMaxGroupCols) return OT_ERR_UNSUPPORTED;
+    if (!ptr_on_device(C[t])) return OT_ERR_ARG;  // host data would need staging memory
+    const int sh = table[algo][bucket_of(m[t])];
+    if (group_smem_bytes(group_shape(sh), algo, n[t], m[t]) > group_smem_limit()) return OT_ERR_UNSUPPORTED;
+    hbucket[t] = sh;
+    ++count[sh];
+    nmax[sh] = std::max(nmax[sh], n[t]);
+    mmax[sh] = std::max(mmax[sh], m[t]);
+    Instance& I = hdesc[t];
+    I.C = C[t]; I.ldc = ldc[t]; I.n = n[t]; I.m = m[t];
+    I.row_to_col = row_to_col[t];
+    I.u = u ? u[t] : nullptr;
+    I.v = v ? v[t] : nullptr;
+    I.cost = cost + t;
+    I.status = status ? status + t : S->status + t;
+    I.stats = nullptr;
+  }
+  // launch order: bucket by bucket, largest instances first
+  int off[OT_NUM_GROUP_SHAPES + 1] = {0};
+  for (int b = 0; b < num_group_shapes(); ++b) off[b + 1] = off[b] + count[b];
+  int fill[OT_NUM_GROUP_SHAPES];
+  std::memcpy(fill, off, sizeof(fill));
+  for (int t = 0; t < k; ++t) horder[fill[hbucket[t]]++] = t;
+  for (int b = 0; b < num_group_shapes(); ++b)
+    std::sort(horder + off[b], horder + off[b + 1], [&](int a, int c) {
+      const long long wa = (long long)n[a] * m[a], wc = (long long)n[c] * m[c];
+      return wa != wc ? wa > wc : a < c;
+    });
+
+  // Upload into the static scratch (pageable source: the copy is staged
+  // before the call returns) and clear the work counters.
+  cudaError_t e = cudaMemcpyAsync(S->desc, hdesc, sizeof(Instance) * k, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->order, horder, sizeof(int32_t) * k, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S->work, 0, sizeof(S->work), s);
+  if (e != cudaSuccess) return OT_ERR_CUDA;
+  for (int b = 0; b < num_group_shapes(); ++b) {
+    if (!count[b]) continue;
+    e = launch_group(group_shape(b), algo, S->desc, S->order + off[b], count[b], S->work + b, nmax[b],
+                     mmax[b], 0, s);
+    if (e != cudaSuccess) return OT_ERR_CUDA;
+  }
+  return OT_OK;
+}

@@ -91,6 +91,9 @@ def load(path: str | None = None):
         "ot_tune_lookup": (ctypes.c_int, [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "ot_tune_set": (ctypes.c_int, [vp, i32, i32, i32, i32]),
         "ot_last_call_stats": (ctypes.c_int, [vp, ctypes.POINTER(ot_stats)]),
+        "ot_assign_solve_batched_noalloc": (ctypes.c_int, [i32, pp, ctypes.POINTER(i64),
+                                                           ctypes.POINTER(i32), ctypes.POINTER(i32), i32,
+                                                           pp, vp, pp, pp, vp, vp]),
         "ot_version": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -293,6 +296,21 @@ def ot_tune_lookup(ctx: Context, algo: int, m: int):
     t, k = ctypes.c_int32(), ctypes.c_int32()
     ctx._raise(ctx.lib.ot_tune_lookup(ctx.h, algo, m, ctypes.byref(t), ctypes.byref(k)), "ot_tune_lookup")
     return t.value, k.value
+
+
+OT_NOALLOC_MAX_INSTANCES = 1024
+
+
+def ot_assign_solve_batched_noalloc(args: BatchArgs, algo: int = OT_KM, stream=None) -> int:
+    """Batched solve through the entry point that allocates no device memory
+    (no context; device tensors only; at most OT_NOALLOC_MAX_INSTANCES
+    instances).  Returns the C return code; results land in ``args``."""
+    lib = load()
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    return lib.ot_assign_solve_batched_noalloc(args.k, ctypes.cast(args.cp, pp), args.ldc, args.n, args.m,
+                                               algo, ctypes.cast(args.rp, pp), _ptr(args.cost),
+                                               ctypes.cast(args.up, pp), ctypes.cast(args.vp, pp),
+                                               _ptr(args.status), _stream_handle(stream))
 
 
 def ot_tune_set(ctx: Context, algo: int, m: int, threads_per_instance: int, cols_per_thread: int):
