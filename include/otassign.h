@@ -162,8 +162,10 @@ int ot_tune_lookup(ot_ctx* ctx, int32_t algo, int32_t m, int32_t* threads_per_in
                    int32_t* cols_per_thread);
 
 /* Force the table entry for the bucket containing m (tests, experiments).
- * OT_ERR_UNSUPPORTED if the shape is not compiled in or cannot hold the
- * bucket's widest instance. */
+ * threads_per_instance = cols_per_thread = 0 routes the bucket to the
+ * cluster engine that otherwise takes instances with m > 4096 (lookup
+ * reports 0, 0 for it).  OT_ERR_UNSUPPORTED if the shape is not compiled in
+ * or cannot hold the bucket's widest instance. */
 int ot_tune_set(ot_ctx* ctx, int32_t algo, int32_t m, int32_t threads_per_instance,
                 int32_t cols_per_thread);
 

@@ -166,6 +166,10 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
     if (skip[t]) continue;
     const Instance& I = insts[t];
     int sh = ctx->table[algo][bucket_of(I.m)];
+    if (sh == kLargeEngine) {  // bucket routed to the cluster engine
+      if (unsupported) unsupported->push_back(t);
+      continue;
+    }
     if (sh >= 0 && group_shape(sh).max_cols() < I.m) {
       int def[2][kNumBuckets];
       default_table(def);
@@ -345,10 +349,15 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
     }
     std::vector<int> unsup;
     if (int rc = run_device_batch(ctx, ctx->api, insts, skip, algo, stream, true, true, &unsup); rc) return rc;
-    for (int t : unsup) st[t] = OT_ERR_UNSUPPORTED;
     ctx->last_k = k;
     ctx->last_skip = skip;
-    for (int t : unsup) ctx->last_skip[t] = 1;
+    // instances wider than a group: the cluster engine, one at a time
+    for (int t : unsup) {
+      if (insts[t].m > large_max_cols()) { st[t] = OT_ERR_UNSUPPORTED; ctx->last_skip[t] = 1; continue; }
+      const int rc = solve_large(ctx, insts[t], algo, stream, nullptr);
+      if (rc == OT_ERR_TIMEOUT || rc == OT_ERR_UNSUPPORTED) { st[t] = rc; continue; }
+      if (rc != OT_OK) return rc;
+    }
     // empty instances: cost 0, status per validation; zero v of width m
     for (int t = 0; t < k; ++t) {
       if (n[t] == 0 && st[t] == OT_OK) {
@@ -446,9 +455,17 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
   }
   std::vector<int> unsup;
   if (int rc = run_device_batch(ctx, ctx->api, insts, skip, algo, stream, true, true, &unsup); rc) return rc;
-  for (int t : unsup) { st[t] = OT_ERR_UNSUPPORTED; skip[t] = 1; }
   ctx->last_k = k;
   ctx->last_skip = skip;
+  std::vector<int> still;
+  for (int t : unsup) {
+    if (insts[t].m > large_max_cols()) { still.push_back(t); continue; }
+    const int rc = solve_large(ctx, insts[t], algo, stream, nullptr);
+    if (rc == OT_ERR_TIMEOUT || rc == OT_ERR_UNSUPPORTED) { st[t] = rc; skip[t] = 1; continue; }
+    if (rc != OT_OK) return rc;
+  }
+  unsup.swap(still);
+  for (int t : unsup) { st[t] = OT_ERR_UNSUPPORTED; skip[t] = 1; ctx->last_skip[t] = 1; }
   std::vector<int32_t> hstatus(k, 0);
   if ((e = cudaMemcpyAsync(cost, dcost, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
     return ctx_cuda(ctx, e, "D2H cost");
@@ -563,6 +580,7 @@ void ot_ctx_destroy(ot_ctx* ctx) {
   ctx->d_status.release();
   ctx->d_io.release();
   ctx->d_scratch.release();
+  ctx->d_large.release();
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -648,7 +666,12 @@ int ot_last_call_stats(ot_ctx* ctx, ot_stats* total) {
 
 int ot_tune_lookup(ot_ctx* ctx, int32_t algo, int32_t m, int32_t* tpi, int32_t* k) {
   if (!ctx || (algo != OT_KM && algo != OT_BKM) || m < 0) return OT_ERR_ARG;
-  const int sh = ctx->table[algo][bucket_of(m)];
+  const int sh = m > kMaxGroupCols ? kLargeEngine : ctx->table[algo][bucket_of(m)];
+  if (sh == kLargeEngine) {
+    if (tpi) *tpi = 0;
+    if (k) *k = 0;
+    return OT_OK;
+  }
   if (sh < 0) return OT_ERR_UNSUPPORTED;
   if (tpi) *tpi = group_shape(sh).tpi;
   if (k) *k = group_shape(sh).k;
@@ -657,6 +680,10 @@ int ot_tune_lookup(ot_ctx* ctx, int32_t algo, int32_t m, int32_t* tpi, int32_t* 
 
 int ot_tune_set(ot_ctx* ctx, int32_t algo, int32_t m, int32_t tpi, int32_t k) {
   if (!ctx || (algo != OT_KM && algo != OT_BKM) || m < 0) return OT_ERR_ARG;
+  if (tpi == 0 && k == 0) {  // route the bucket to the cluster engine
+    ctx->table[algo][bucket_of(m)] = kLargeEngine;
+    return OT_OK;
+  }
   const int sh = shape_index(tpi, k);
   const int b = bucket_of(m);
   if (sh < 0 || group_shape(sh).max_cols() < (32 << b) || m > kMaxGroupCols)

@@ -20,6 +20,7 @@ namespace ot {
 constexpr int kNumBuckets = 8;        // bucket b: m <= 32 << b
 constexpr int kMaxGroupCols = 4096;   // widest instance one group engine handles
 constexpr int kForkStreams = 4;
+constexpr int kLargeEngine = -2;  // table entry: use the cluster engine
 int bucket_of(int m);
 int shape_index(int tpi, int k);
 void default_table(int table[2][kNumBuckets]);
@@ -67,7 +68,7 @@ struct ot_ctx {
   std::mutex api_mu;
 
   LaunchSlot api;
-  DevBuf d_status, d_io, d_scratch;
+  DevBuf d_status, d_io, d_scratch, d_large;
 
   int table[2][ot::kNumBuckets];
   std::string tune_file;
@@ -90,5 +91,9 @@ void load_tune_file(ot_ctx* ctx);
 int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<ot::Instance>& insts,
                      const std::vector<int>& skip, int algo, cudaStream_t stream, bool fork,
                      bool own_stats, std::vector<int>* unsupported);
+// Wide-instance engine (ot_large.cu): one instance on a thread-block
+// cluster plus grid-wide passes; synchronises `stream`.
+int solve_large(ot_ctx* ctx, const ot::Instance& I, int algo, cudaStream_t stream, int64_t* stats_out);
+int large_max_cols();
 int serve_init(ot_ctx* ctx, const ot_config& cfg);
 void serve_shutdown(ot_ctx* ctx);
