@@ -139,6 +139,122 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def measure_single_16384(ctx, stream, ot, torch):
+    """n = m = 16384 (1024 x 1024 grid, squared distances, 1 GiB int32):
+    batched KM solve time and effective cost-matrix bandwidth."""
+    C = W.single_16384()
+    Cd = torch.from_numpy(C).cuda()
+    del C
+    torch.cuda.synchronize()
+    peak, kind = _peaks()
+    best = None
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r, c, u, v, st = ot.ot_assign_solve_stats(ctx, Cd, ot.OT_BKM, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1000.0
+        if best is None or t < best[0]:
+            best = (t, st, int(c.item()))
+    t, st, cost = best
+    alg = st["cost_bytes"] + st["init_bytes"]
+    del Cd
+    torch.cuda.empty_cache()
+    return {"algo": "batched KM", "s_per_solve": t, "solves_per_s": 1.0 / t, "cost": cost,
+            "algorithmic_bytes": alg, "achieved_gbs": alg / t / 1e9,
+            "hbm_frac": alg / t / 1e9 / peak, "peak_gbs": peak, "peak_kind": kind,
+            "hbm_frac_vs_8tbs": alg / t / 1e9 / 8000.0,
+            "steps": st["steps"], "phases": st["phases"], "rows_scanned": st["rows_scanned"]}
+
+
+def measure_served(ctx_unused, stream, ot, torch, dev, args):
+    """Open-loop Poisson stream of MNIST-like requests (n log-uniform in
+    [16, 2048], squared pixel distances on a 28 x 28 grid) through
+    ot_assign_submit / ot_assign_poll, at 0.5x and 0.9x of the measured
+    saturated throughput; p50/p99 latency from arrival to completion."""
+    import threading
+    nreq = args.served_requests
+    reqs = W.served_requests(nreq, rate_per_s=1.0, seed=W.BASE_SEED + 7)
+    mats = [torch.from_numpy(C).pin_memory() for _, C in reqs]
+    outs = [(torch.empty(C.shape[0], dtype=torch.int32), torch.empty(1, dtype=torch.int64), None, None)
+            for C in mats]
+
+    tune_path = os.path.join(ROOT, "_build_served_tune.jsonl")
+    if os.path.exists(tune_path):
+        os.remove(tune_path)
+    tctx = ot.Context(tune_file=tune_path)
+    sample = [m.to(dev) for m in mats[:256]]
+    ot.ot_autotune(tctx, sample, ot.OT_AUTO, repeats=1)
+    tctx.close()
+    del sample
+
+    def run(rate):
+        sctx = ot.Context(hbm_budget_bytes=8 << 30, wave_streams=4, tune_file=tune_path)
+        arrivals = [t / rate for t, _ in reqs] if rate else [0.0] * nreq
+        done_t = [None] * nreq
+        tickets = [None] * nreq
+        t0 = time.perf_counter()
+        stop = [False]
+
+        def submitter():
+            for i in range(nreq):
+                if rate:
+                    d = arrivals[i] - (time.perf_counter() - t0)
+                    if d > 0:
+                        time.sleep(d)
+                tickets[i] = ot.ot_assign_submit(sctx, mats[i], ot.OT_AUTO)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        pending = 0
+        nxt = 0
+        live = []
+        while nxt < nreq or live:
+            while nxt < nreq and tickets[nxt] is not None:
+                live.append(nxt)
+                nxt += 1
+            rest = []
+            for i in live:
+                if ot.ot_assign_poll(sctx, tickets[i], outs[i]) == ot.OT_OK:
+                    done_t[i] = time.perf_counter() - t0
+                else:
+                    rest.append(i)
+            live = rest
+            if nxt < nreq and not live:
+                time.sleep(0.0001)
+        th.join()
+        total = time.perf_counter() - t0
+        cnt = ot.ot_serving_counters(sctx)
+        sctx.close()
+        arr = np.array(arrivals) if rate else np.zeros(nreq)
+        lat = np.array(done_t) - arr
+        return {"rate_per_s": rate, "solves_per_s": nreq / total, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "waves": cnt["waves"],
+                "max_concurrent_waves": cnt["max_concurrent_waves"]}
+
+    sat = run(None)
+    res = {"requests": nreq, "n": "log-uniform [16, 2048]", "saturated": sat}
+    for f in (0.5, 0.9):
+        res[f"at_{f}x"] = run(f * sat["solves_per_s"])
+    # plain: one ot_assign_solve per request on the device, no batching
+    dmats = [m.to(dev) for m in mats[: min(64, nreq)]]
+    ctx = ot.Context()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    lats = []
+    for C in dmats:
+        a = time.perf_counter()
+        r, c, u, v = ot.ot_assign_solve(ctx, C, ot.OT_KM, stream)
+        torch.cuda.synchronize()
+        lats.append(time.perf_counter() - a)
+    tp = time.perf_counter() - t
+    ctx.close()
+    res["plain_gpu_km"] = {"solves_per_s": len(dmats) / tp, "p50_solve_ms": float(np.median(lats) * 1e3),
+                           "p99_solve_ms": float(np.percentile(lats, 99) * 1e3), "sample": len(dmats)}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -149,8 +265,10 @@ def main():
     ap.add_argument("--sample", type=int, default=96)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--skip-extras", action="store_true")
-    ap.add_argument("--profile-once", action="store_true",
-                    help="untimed: 2 warm-up batched KM launches then 1 more, for an ncu capture")
+    ap.add_argument("--served-requests", type=int, default=1500)
+    ap.add_argument("--profile-once", default=None, choices=["batch", "n16384", "n8192"],
+                    help="untimed single run for an ncu capture: 'batch' = 3 batched KM calls on the "
+                         "4096-instance batch; 'n16384' / 'n8192' = one batched-KM solve on a grid instance")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -177,6 +295,14 @@ def main():
     ctx = ot.Context(device=local)
     stream = torch.cuda.current_stream()
 
+    if args.profile_once in ("n16384", "n8192"):
+        n = 16384 if args.profile_once == "n16384" else 8192
+        C = W.grid_sqdist(n, n, grid=1024 if n == 16384 else 724)
+        r, c, u, v, st = ot.ot_assign_solve_stats(ctx, torch.from_numpy(C).to(dev), ot.OT_BKM, stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_once": args.profile_once, "cost": int(c.item()), **st}))
+        ctx.close()
+        return
     Cs = batch_for_rank(rank, args.k)
     dC = [torch.from_numpy(C).to(dev) for C in Cs]
     if args.profile_once:
@@ -191,22 +317,11 @@ def main():
     d2h_bytes = sum(C.shape[0] * 4 + C.shape[0] * 8 + C.shape[1] * 8 + 8 for C in Cs)
     torch.cuda.synchronize()
 
-    # pick the faster algorithm for the batch (autotuned shapes)
-    best_algo, best_t = None, 1e30
-    for algo in (ot.OT_KM, ot.OT_BKM):
-        ot.ot_autotune(ctx, dC, algo, repeats=1)
-        a = ot.BatchArgs(dC)
-        ot.ot_assign_solve_batched(ctx, a, algo, stream)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ot.ot_assign_solve_batched(ctx, a, algo, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1)
-        if t < best_t:
-            best_algo, best_t = algo, t
-    algo = best_algo
+    # autotune shape and algorithm (KM or batched KM) per size bucket on
+    # this batch; OT_AUTO then uses the faster exact algorithm per bucket
+    ot.ot_autotune(ctx, dC, ot.OT_AUTO, repeats=1)
+    algo = ot.OT_AUTO
+    tuned = {m: ot.ot_tune_lookup(ctx, ot.OT_AUTO, m) for m in (32, 64, 128, 256)}
     args_dev = ot.BatchArgs(dC)
 
     def barrier():
@@ -287,7 +402,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": "batch4096_embed300_n32-256", "instances_per_gpu": args.k,
-                       "algo": "KM" if algo == ot.OT_KM else "batched KM",
+                       "algo": "auto (tuned per bucket)",
+                       "tuned_shapes": {str(m): list(v) for m, v in tuned.items()},
                        "cost_bytes_resident": h2d_bytes, "l2": "inputs larger than L2 (%.0f MB > 129 MB)" % (h2d_bytes / 1e6),
                        "parallelism": f"replicas x{world} (instances sharded, no collective)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -321,6 +437,10 @@ def main():
         rate, done, dt = cpu_oracle_rate(Cs, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"first {done} instances of the batch, oracle KM single-threaded, {dt:.1f}s"}
+        del Cs, dC, args_dev, args_host, hC, houts, slabC
+        torch.cuda.empty_cache()
+        line["single_16384"] = measure_single_16384(ctx, stream, ot, torch)
+        line["served"] = measure_served(ctx, stream, ot, torch, dev, args)
     elif rank == 0:
         line["cpu_baseline"] = None
     if rank == 0:

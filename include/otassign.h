@@ -64,6 +64,9 @@ extern "C" {
 
 #define OT_KM 0
 #define OT_BKM 1
+#define OT_AUTO 2   /* per size bucket, whichever of OT_KM / OT_BKM the tuned table
+                       names (built-in: KM for m <= 256, batched KM above); both are
+                       exact, the optimal assignment and duals returned depend on it */
 
 /* Per-solve counters, written by ot_assign_solve_stats. */
 typedef struct ot_stats {
@@ -151,8 +154,9 @@ int ot_serving_counters(ot_ctx* ctx, int64_t* out8);
  * pointers, as in ot_assign_solve_batched), time each compiled group shape
  * `repeats` times on exactly those instances and keep the fastest shape for
  * that bucket and algorithm in the context's table (also appended to
- * cfg->tune_file when one was given).  Results are written to scratch and
- * discarded.  Returns OT_OK or an error code. */
+ * cfg->tune_file when one was given); with algo = OT_AUTO both algorithms
+ * are timed and the faster becomes the bucket's OT_AUTO choice.  Results are
+ * written to scratch and discarded.  Returns OT_OK or an error code. */
 int ot_autotune(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* ldc,
                 const int32_t* n, const int32_t* m, int32_t algo, int32_t repeats);
 
@@ -164,7 +168,8 @@ int ot_tune_lookup(ot_ctx* ctx, int32_t algo, int32_t m, int32_t* threads_per_in
 /* Force the table entry for the bucket containing m (tests, experiments).
  * threads_per_instance = cols_per_thread = 0 routes the bucket to the
  * cluster engine that otherwise takes instances with m > 4096 (lookup
- * reports 0, 0 for it).  OT_ERR_UNSUPPORTED if the shape is not compiled in
+ * reports 0, 0 for it).  With algo = OT_AUTO, threads_per_instance names the
+ * algorithm (OT_KM or OT_BKM) that OT_AUTO uses for the bucket.  OT_ERR_UNSUPPORTED if the shape is not compiled in
  * or cannot hold the bucket's widest instance. */
 int ot_tune_set(ot_ctx* ctx, int32_t algo, int32_t m, int32_t threads_per_instance,
                 int32_t cols_per_thread);
@@ -189,7 +194,8 @@ int ot_tune_set(ot_ctx* ctx, int32_t algo, int32_t m, int32_t threads_per_instan
  *     (different streams or threads) race: serialise them;
  *   - the first call on a device looks up the array's device address and may
  *     load the module; make that first call before any stream capture.
- * Results are identical to ot_assign_solve_batched's.  Asynchronous on
+ * OT_AUTO resolves with the built-in table.  Results are identical to
+ * ot_assign_solve_batched's with a context that has the built-in table.  Asynchronous on
  * `stream` (NULL = the legacy default stream); per-instance device status
  * codes go to status[k] when it is non-NULL. */
 #define OT_NOALLOC_MAX_INSTANCES 1024

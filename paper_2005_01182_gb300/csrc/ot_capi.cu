@@ -64,9 +64,21 @@ void default_table(int table[2][kNumBuckets]) {
     for (int b = 0; b < kNumBuckets; ++b) table[a][b] = shape_index(tpi[b], kk[b]);
 }
 
+void default_auto(int auto_algo[kNumBuckets]) {
+  // KM for the small buckets, batched KM from m > 256 on (fewer dependent
+  // steps per instance); the autotuner may change either
+  for (int b = 0; b < kNumBuckets; ++b) auto_algo[b] = b <= 3 ? kAlgoKM : kAlgoBKM;
+}
+
 }  // namespace ot
 
 using namespace ot;
+
+int resolve_algo(const ot_ctx* ctx, int algo, int m) {
+  if (algo != OT_AUTO) return algo;
+  if (m > kMaxGroupCols) return kAlgoBKM;
+  return ctx->auto_algo[bucket_of(m)];
+}
 
 // ---------------------------------------------------------------------------
 // helpers
@@ -144,6 +156,7 @@ static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Bucket {
   int shape;
+  int algo = 0;
   int nmax = 0, mmax = 0;
   std::vector<int> idx;
 };
@@ -160,12 +173,13 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
     for (int t = 0; t < k; ++t) insts[t].stats = dstats + size_t(t) * 8;
   }
 
-  // bucket by tuned shape
+  // bucket by (algorithm, tuned shape)
   std::map<int, Bucket> buckets;
   for (int t = 0; t < k; ++t) {
     if (skip[t]) continue;
     const Instance& I = insts[t];
-    int sh = ctx->table[algo][bucket_of(I.m)];
+    const int ia = resolve_algo(ctx, algo, I.m);
+    int sh = ctx->table[ia][bucket_of(I.m)];
     if (sh == kLargeEngine) {  // bucket routed to the cluster engine
       if (unsupported) unsupported->push_back(t);
       continue;
@@ -173,15 +187,16 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
     if (sh >= 0 && group_shape(sh).max_cols() < I.m) {
       int def[2][kNumBuckets];
       default_table(def);
-      sh = def[algo][bucket_of(I.m)];
+      sh = def[ia][bucket_of(I.m)];
     }
     if (I.m > kMaxGroupCols || sh < 0 ||
-        group_smem_bytes(group_shape(sh), algo, I.n, I.m) > group_smem_limit()) {
+        group_smem_bytes(group_shape(sh), ia, I.n, I.m) > group_smem_limit()) {
       if (unsupported) unsupported->push_back(t);
       continue;
     }
-    Bucket& b = buckets[sh];
+    Bucket& b = buckets[ia * 64 + sh];
     b.shape = sh;
+    b.algo = ia;
     b.nmax = std::max(b.nmax, I.n);
     b.mmax = std::max(b.mmax, I.m);
     b.idx.push_back(t);
@@ -223,7 +238,7 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
     Bucket& b = kv.second;
     offs.push_back(off);
     for (int t : b.idx) horder[off++] = t;
-    key += "|" + std::to_string(b.shape) + "," + std::to_string(b.idx.size()) + "," +
+    key += "|" + std::to_string(b.algo) + ":" + std::to_string(b.shape) + "," + std::to_string(b.idx.size()) + "," +
            std::to_string(b.nmax) + "," + std::to_string(b.mmax);
   }
   key += "|" + std::to_string(reinterpret_cast<uintptr_t>(stream));
@@ -239,7 +254,7 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
       int bi = 0;
       for (auto& kv : buckets) {
         Bucket& b = kv.second;
-        e = launch_group(group_shape(b.shape), algo, dinst, dorder + offs[bi], int(b.idx.size()),
+        e = launch_group(group_shape(b.shape), b.algo, dinst, dorder + offs[bi], int(b.idx.size()),
                          dwork + bi, b.nmax, b.mmax, 0, s);
         if (e != cudaSuccess) return e;
         ++bi;
@@ -252,7 +267,7 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
       Bucket& b = kv.second;
       cudaStream_t bs = ctx->bstreams[bi % kForkStreams];
       if ((e = cudaStreamWaitEvent(bs, ctx->fork_ev, 0)) != cudaSuccess) return e;
-      e = launch_group(group_shape(b.shape), algo, dinst, dorder + offs[bi], int(b.idx.size()),
+      e = launch_group(group_shape(b.shape), b.algo, dinst, dorder + offs[bi], int(b.idx.size()),
                        dwork + bi, b.nmax, b.mmax, 0, bs);
       if (e != cudaSuccess) return e;
       ++bi;
@@ -310,7 +325,7 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
                       const int32_t* n, const int32_t* m, int algo, int32_t* const* r2c,
                       int64_t* cost, int64_t* const* u, int64_t* const* v, int32_t* status,
                       cudaStream_t stream, ot_stats* stats_out) {
-  if (algo != OT_KM && algo != OT_BKM) return ctx_fail(ctx, OT_ERR_ARG, "bad algo");
+  if (algo != OT_KM && algo != OT_BKM && algo != OT_AUTO) return ctx_fail(ctx, OT_ERR_ARG, "bad algo");
   if (k < 0) return ctx_fail(ctx, OT_ERR_ARG, "k < 0");
   if (k == 0) return OT_OK;
   if (!C || !ldc || !n || !m || !r2c || !cost) return ctx_fail(ctx, OT_ERR_ARG, "null array");
@@ -354,7 +369,7 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
     // instances wider than a group: the cluster engine, one at a time
     for (int t : unsup) {
       if (insts[t].m > large_max_cols()) { st[t] = OT_ERR_UNSUPPORTED; ctx->last_skip[t] = 1; continue; }
-      const int rc = solve_large(ctx, insts[t], algo, stream, nullptr);
+      const int rc = solve_large(ctx, insts[t], resolve_algo(ctx, algo, insts[t].m), stream, nullptr);
       if (rc == OT_ERR_TIMEOUT || rc == OT_ERR_UNSUPPORTED) { st[t] = rc; continue; }
       if (rc != OT_OK) return rc;
     }
@@ -460,7 +475,7 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
   std::vector<int> still;
   for (int t : unsup) {
     if (insts[t].m > large_max_cols()) { still.push_back(t); continue; }
-    const int rc = solve_large(ctx, insts[t], algo, stream, nullptr);
+    const int rc = solve_large(ctx, insts[t], resolve_algo(ctx, algo, insts[t].m), stream, nullptr);
     if (rc == OT_ERR_TIMEOUT || rc == OT_ERR_UNSUPPORTED) { st[t] = rc; skip[t] = 1; continue; }
     if (rc != OT_OK) return rc;
   }
@@ -556,6 +571,7 @@ int ot_ctx_create(ot_ctx** out, const ot_config* cfg) {
   if (ctx->api.init() != OT_OK) { ot_ctx_destroy(ctx); return OT_ERR_CUDA; }
   ctx->api.use_graphs = true;
   default_table(ctx->table);
+  default_auto(ctx->auto_algo);
   if (c.tune_file) {
     ctx->tune_file = c.tune_file;
     load_tune_file(ctx);
@@ -665,7 +681,8 @@ int ot_last_call_stats(ot_ctx* ctx, ot_stats* total) {
 }
 
 int ot_tune_lookup(ot_ctx* ctx, int32_t algo, int32_t m, int32_t* tpi, int32_t* k) {
-  if (!ctx || (algo != OT_KM && algo != OT_BKM) || m < 0) return OT_ERR_ARG;
+  if (!ctx || (algo != OT_KM && algo != OT_BKM && algo != OT_AUTO) || m < 0) return OT_ERR_ARG;
+  algo = resolve_algo(ctx, algo, m);
   const int sh = m > kMaxGroupCols ? kLargeEngine : ctx->table[algo][bucket_of(m)];
   if (sh == kLargeEngine) {
     if (tpi) *tpi = 0;
@@ -679,7 +696,12 @@ int ot_tune_lookup(ot_ctx* ctx, int32_t algo, int32_t m, int32_t* tpi, int32_t* 
 }
 
 int ot_tune_set(ot_ctx* ctx, int32_t algo, int32_t m, int32_t tpi, int32_t k) {
-  if (!ctx || (algo != OT_KM && algo != OT_BKM) || m < 0) return OT_ERR_ARG;
+  if (!ctx || (algo != OT_KM && algo != OT_BKM && algo != OT_AUTO) || m < 0) return OT_ERR_ARG;
+  if (algo == OT_AUTO) {  // tpi selects the algorithm OT_AUTO uses for this bucket
+    if (tpi != OT_KM && tpi != OT_BKM) return ctx_fail(ctx, OT_ERR_ARG, "auto entry must name KM or BKM");
+    ctx->auto_algo[bucket_of(m)] = tpi;
+    return OT_OK;
+  }
   if (tpi == 0 && k == 0) {  // route the bucket to the cluster engine
     ctx->table[algo][bucket_of(m)] = kLargeEngine;
     return OT_OK;
@@ -695,7 +717,7 @@ int ot_tune_set(ot_ctx* ctx, int32_t algo, int32_t m, int32_t tpi, int32_t k) {
 int ot_autotune(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* ldc,
                 const int32_t* n, const int32_t* m, int32_t algo, int32_t repeats) {
   if (!ctx) return OT_ERR_ARG;
-  if ((algo != OT_KM && algo != OT_BKM) || k <= 0 || !C || !ldc || !n || !m)
+  if ((algo != OT_KM && algo != OT_BKM && algo != OT_AUTO) || k <= 0 || !C || !ldc || !n || !m)
     return ctx_fail(ctx, OT_ERR_ARG, "bad arguments");
   cudaSetDevice(ctx->device);
   repeats = std::max(1, repeats);
@@ -749,35 +771,46 @@ int ot_autotune(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* 
       return (long long)n[a] * m[a] > (long long)n[c] * m[c];
     });
     cudaMemcpyAsync(dorder, idx.data(), sizeof(int32_t) * idx.size(), cudaMemcpyHostToDevice, s);
-    int best = -1;
-    float best_ms = 1e30f;
-    for (int sh = 0; sh < num_group_shapes(); ++sh) {
-      GroupShape g = group_shape(sh);
-      if (g.max_cols() < mmax || g.max_cols() > 8 * std::max(mmax, 32)) continue;
-      if (group_smem_bytes(g, algo, nmax, mmax) > group_smem_limit()) continue;
-      float tmin = 1e30f;
-      bool ok = true;
-      for (int r = 0; r < repeats + 1 && ok; ++r) {
-        cudaMemsetAsync(dwork, 0, sizeof(int), s);
-        cudaEventRecord(e0, s);
-        if (launch_group(g, algo, dinst, dorder, int(idx.size()), dwork, nmax, mmax, 0, s) != cudaSuccess) {
-          cudaGetLastError();
-          ok = false;
-          break;
+    // OT_AUTO tunes both algorithms and keeps the faster for the bucket
+    int best_algo = -1;
+    float best_algo_ms = 1e30f;
+    for (int a = 0; a < 2; ++a) {
+      if (algo != OT_AUTO && a != algo) continue;
+      int best = -1;
+      float best_ms = 1e30f;
+      for (int sh = 0; sh < num_group_shapes(); ++sh) {
+        GroupShape g = group_shape(sh);
+        if (g.max_cols() < mmax || g.max_cols() > 8 * std::max(mmax, 32)) continue;
+        if (group_smem_bytes(g, a, nmax, mmax) > group_smem_limit()) continue;
+        float tmin = 1e30f;
+        bool ok = true;
+        for (int r = 0; r < repeats + 1 && ok; ++r) {
+          cudaMemsetAsync(dwork, 0, sizeof(int), s);
+          cudaEventRecord(e0, s);
+          if (launch_group(g, a, dinst, dorder, int(idx.size()), dwork, nmax, mmax, 0, s) != cudaSuccess) {
+            cudaGetLastError();
+            ok = false;
+            break;
+          }
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (r > 0) tmin = std::min(tmin, ms);  // first run warms up
         }
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (r > 0) tmin = std::min(tmin, ms);  // first run warms up
+        if (ok && tmin < best_ms) { best_ms = tmin; best = sh; }
       }
-      if (ok && tmin < best_ms) { best_ms = tmin; best = sh; }
+      if (best >= 0) {
+        ctx->table[a][kv.first] = best;
+        if (tf)
+          std::fprintf(tf, "{\"algo\": %d, \"bucket_mmax\": %d, \"tpi\": %d, \"k\": %d, \"ms\": %.4f}\n",
+                       a, 32 << kv.first, group_shape(best).tpi, group_shape(best).k, best_ms);
+        if (best_ms < best_algo_ms) { best_algo_ms = best_ms; best_algo = a; }
+      }
     }
-    if (best >= 0) {
-      ctx->table[algo][kv.first] = best;
-      if (tf)
-        std::fprintf(tf, "{\"algo\": %d, \"bucket_mmax\": %d, \"tpi\": %d, \"k\": %d, \"ms\": %.4f}\n",
-                     algo, 32 << kv.first, group_shape(best).tpi, group_shape(best).k, best_ms);
+    if (algo == OT_AUTO && best_algo >= 0) {
+      ctx->auto_algo[kv.first] = best_algo;
+      if (tf) std::fprintf(tf, "{\"auto\": %d, \"bucket_mmax\": %d, \"ms\": %.4f}\n", best_algo, 32 << kv.first, best_algo_ms);
     }
   }
   if (tf) std::fclose(tf);
@@ -803,8 +836,11 @@ void load_tune_file(ot_ctx* ctx) {
     if ((p = std::strstr(line, "\"bucket_mmax\":"))) mm = std::atoi(p + 14);
     if ((p = std::strstr(line, "\"tpi\":"))) tpi = std::atoi(p + 6);
     if ((p = std::strstr(line, "\"k\":"))) kk = std::atoi(p + 4);
+    int au = -1;
+    if ((p = std::strstr(line, "\"auto\":"))) au = std::atoi(p + 7);
     const int sh = shape_index(tpi, kk);
     if ((a == 0 || a == 1) && mm > 0 && sh >= 0) ctx->table[a][bucket_of(mm)] = sh;
+    if ((au == 0 || au == 1) && mm > 0) ctx->auto_algo[bucket_of(mm)] = au;
   }
   std::fclose(f);
 }

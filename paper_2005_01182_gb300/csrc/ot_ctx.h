@@ -24,6 +24,7 @@ constexpr int kLargeEngine = -2;  // table entry: use the cluster engine
 int bucket_of(int m);
 int shape_index(int tpi, int k);
 void default_table(int table[2][kNumBuckets]);
+void default_auto(int auto_algo[kNumBuckets]);
 }  // namespace ot
 
 struct DevBuf {
@@ -71,6 +72,7 @@ struct ot_ctx {
   DevBuf d_status, d_io, d_scratch, d_large;
 
   int table[2][ot::kNumBuckets];
+  int auto_algo[ot::kNumBuckets];  // algorithm OT_AUTO resolves to, per bucket
   std::string tune_file;
 
   int last_k = 0;               // instances of the most recent API call
@@ -95,5 +97,7 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<ot::Instance>& i
 // cluster plus grid-wide passes; synchronises `stream`.
 int solve_large(ot_ctx* ctx, const ot::Instance& I, int algo, cudaStream_t stream, int64_t* stats_out);
 int large_max_cols();
+// OT_KM / OT_BKM unchanged; OT_AUTO -> the tuned algorithm of m's bucket.
+int resolve_algo(const ot_ctx* ctx, int algo, int m);
 int serve_init(ot_ctx* ctx, const ot_config& cfg);
 void serve_shutdown(ot_ctx* ctx);

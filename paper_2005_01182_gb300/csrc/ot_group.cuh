@@ -44,14 +44,19 @@ __device__ __forceinline__ bool lex_less(long long d1, int j1, long long d2, int
   return d1 < d2 || (d1 == d2 && j1 < j2);
 }
 
+// Lexicographic (d, j) minimum over the warp with three 32-bit warp
+// reductions (redux.sync): flipping the sign bit makes the int64 order an
+// unsigned order, then the high word, the low word among lanes holding the
+// minimal high word, and the column among lanes holding the minimal key are
+// reduced in turn.  Every lane receives the result.
 __device__ __forceinline__ Best warp_argmin(Best b) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    long long d2 = __shfl_xor_sync(0xffffffffu, b.d, o);
-    int j2 = __shfl_xor_sync(0xffffffffu, b.j, o);
-    if (lex_less(d2, j2, b.d, b.j)) { b.d = d2; b.j = j2; }
-  }
-  return b;
+  const unsigned long long key = static_cast<unsigned long long>(b.d) ^ 0x8000000000000000ull;
+  const unsigned hi = unsigned(key >> 32), lo = unsigned(key);
+  const unsigned mh = __reduce_min_sync(0xffffffffu, hi);
+  const unsigned ml = __reduce_min_sync(0xffffffffu, hi == mh ? lo : 0xffffffffu);
+  const unsigned mj = __reduce_min_sync(0xffffffffu, (hi == mh && lo == ml) ? unsigned(b.j) : 0xffffffffu);
+  const unsigned long long mk = (static_cast<unsigned long long>(mh) << 32) | ml;
+  return Best{static_cast<long long>(mk ^ 0x8000000000000000ull), int(mj)};
 }
 
 __device__ __forceinline__ long long warp_sum(long long x) {
@@ -225,8 +230,8 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
         if (t == 0) S.misc[p ^ 1] = 0;
       }
       // A1 / B2: scan the rows that just joined the tree, columns outside T
-      for (int q = 0; q < L; ++q) {
-        const int i = (ALGO == kAlgoKM) ? km_row : S.list[q];
+      if constexpr (ALGO == kAlgoKM) {
+        const int i = km_row;
         const long long base = level - S.u[i];
         const int32_t* row = C + i * ldc;
 #pragma unroll
@@ -234,9 +239,49 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
           const int j = t + k * TPI;
           if (j < m && !((inT >> k) & 1u)) {
             const long long cand = base + __ldg(row + j) - v[k];
-            if (cand < dist[k] || (ALGO == kAlgoBKM && cand == dist[k] && i < pred[k])) {
+            if (cand < dist[k]) {
               dist[k] = cand;
               pred[k] = i;
+            }
+          }
+        }
+      } else {
+        // two rows per iteration so that their loads are in flight together
+        int q = 0;
+        for (; q + 2 <= L; q += 2) {
+          const int i0 = S.list[q], i1 = S.list[q + 1];
+          const long long b0 = level - S.u[i0], b1 = level - S.u[i1];
+          const int32_t* r0 = C + i0 * ldc;
+          const int32_t* r1 = C + i1 * ldc;
+          int c0[K], c1[K];
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const int j = t + k * TPI;
+            const bool live = j < m && !((inT >> k) & 1u);
+            c0[k] = live ? __ldg(r0 + j) : 0;
+            c1[k] = live ? __ldg(r1 + j) : 0;
+          }
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const int j = t + k * TPI;
+            if (j < m && !((inT >> k) & 1u)) {
+              const long long x0 = b0 + c0[k] - v[k];
+              if (x0 < dist[k] || (x0 == dist[k] && i0 < pred[k])) { dist[k] = x0; pred[k] = i0; }
+              const long long x1 = b1 + c1[k] - v[k];
+              if (x1 < dist[k] || (x1 == dist[k] && i1 < pred[k])) { dist[k] = x1; pred[k] = i1; }
+            }
+          }
+        }
+        for (; q < L; ++q) {
+          const int i = S.list[q];
+          const long long base = level - S.u[i];
+          const int32_t* row = C + i * ldc;
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const int j = t + k * TPI;
+            if (j < m && !((inT >> k) & 1u)) {
+              const long long cand = base + __ldg(row + j) - v[k];
+              if (cand < dist[k] || (cand == dist[k] && i < pred[k])) { dist[k] = cand; pred[k] = i; }
             }
           }
         }

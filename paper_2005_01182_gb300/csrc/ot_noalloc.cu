@@ -63,7 +63,7 @@ extern "C" int ot_assign_solve_batched_noalloc(int32_t k, const int32_t* const* 
                                                int32_t* const* row_to_col, int64_t* cost,
                                                int64_t* const* u, int64_t* const* v, int32_t* status,
                                                void* stream) {
-  if (algo != OT_KM && algo != OT_BKM) return OT_ERR_ARG;
+  if (algo != OT_KM && algo != OT_BKM && algo != OT_AUTO) return OT_ERR_ARG;
   if (k < 0 || (k > 0 && (!C || !ldc || !n || !m || !row_to_col || !cost))) return OT_ERR_ARG;
   if (k > kNoAllocMaxInstances) return OT_ERR_UNSUPPORTED;  // beyond the static scratch
   if (k == 0) return OT_OK;
@@ -79,20 +79,23 @@ extern "C" int ot_assign_solve_batched_noalloc(int32_t k, const int32_t* const* 
   Instance hdesc[kNoAllocMaxInstances];
   int32_t horder[kNoAllocMaxInstances];
   int32_t hbucket[kNoAllocMaxInstances];
-  int table[2][kNumBuckets];
+  int table[2][kNumBuckets], auto_algo[kNumBuckets];
   default_table(table);
-  int count[OT_NUM_GROUP_SHAPES] = {0}, nmax[OT_NUM_GROUP_SHAPES] = {0},
-      mmax[OT_NUM_GROUP_SHAPES] = {0};
+  default_auto(auto_algo);
+  // launch buckets: (algorithm, shape)
+  constexpr int NB = 2 * OT_NUM_GROUP_SHAPES;
+  int count[NB] = {0}, nmax[NB] = {0}, mmax[NB] = {0};
   for (int t = 0; t < k; ++t) {
     if (n[t] < 1 || m[t] < n[t] || ldc[t] < m[t] || !C[t] || !row_to_col[t]) return OT_ERR_ARG;
     if (m[t] > kMaxGroupCols) return OT_ERR_UNSUPPORTED;
     if (!ptr_on_device(C[t])) return OT_ERR_ARG;  // host data would need staging memory
-    const int sh = table[algo][bucket_of(m[t])];
-    if (group_smem_bytes(group_shape(sh), algo, n[t], m[t]) > group_smem_limit()) return OT_ERR_UNSUPPORTED;
-    hbucket[t] = sh;
-    ++count[sh];
-    nmax[sh] = std::max(nmax[sh], n[t]);
-    mmax[sh] = std::max(mmax[sh], m[t]);
+    const int ia = algo == OT_AUTO ? auto_algo[bucket_of(m[t])] : algo;
+    const int sh = table[ia][bucket_of(m[t])];
+    if (group_smem_bytes(group_shape(sh), ia, n[t], m[t]) > group_smem_limit()) return OT_ERR_UNSUPPORTED;
+    hbucket[t] = ia * OT_NUM_GROUP_SHAPES + sh;
+    ++count[hbucket[t]];
+    nmax[hbucket[t]] = std::max(nmax[hbucket[t]], n[t]);
+    mmax[hbucket[t]] = std::max(mmax[hbucket[t]], m[t]);
     Instance& I = hdesc[t];
     I.C = C[t]; I.ldc = ldc[t]; I.n = n[t]; I.m = m[t];
     I.row_to_col = row_to_col[t];
@@ -103,12 +106,12 @@ extern "C" int ot_assign_solve_batched_noalloc(int32_t k, const int32_t* const* 
     I.stats = nullptr;
   }
   // launch order: bucket by bucket, largest instances first
-  int off[OT_NUM_GROUP_SHAPES + 1] = {0};
-  for (int b = 0; b < num_group_shapes(); ++b) off[b + 1] = off[b] + count[b];
-  int fill[OT_NUM_GROUP_SHAPES];
+  int off[NB + 1] = {0};
+  for (int b = 0; b < NB; ++b) off[b + 1] = off[b] + count[b];
+  int fill[NB];
   std::memcpy(fill, off, sizeof(fill));
   for (int t = 0; t < k; ++t) horder[fill[hbucket[t]]++] = t;
-  for (int b = 0; b < num_group_shapes(); ++b)
+  for (int b = 0; b < NB; ++b)
     std::sort(horder + off[b], horder + off[b + 1], [&](int a, int c) {
       const long long wa = (long long)n[a] * m[a], wc = (long long)n[c] * m[c];
       return wa != wc ? wa > wc : a < c;
@@ -120,10 +123,10 @@ extern "C" int ot_assign_solve_batched_noalloc(int32_t k, const int32_t* const* 
   if (e == cudaSuccess) e = cudaMemcpyAsync(S->order, horder, sizeof(int32_t) * k, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(S->work, 0, sizeof(S->work), s);
   if (e != cudaSuccess) return OT_ERR_CUDA;
-  for (int b = 0; b < num_group_shapes(); ++b) {
+  for (int b = 0; b < NB; ++b) {
     if (!count[b]) continue;
-    e = launch_group(group_shape(b), algo, S->desc, S->order + off[b], count[b], S->work + b, nmax[b],
-                     mmax[b], 0, s);
+    e = launch_group(group_shape(b % OT_NUM_GROUP_SHAPES), b / OT_NUM_GROUP_SHAPES, S->desc, S->order + off[b],
+                     count[b], S->work + b, nmax[b], mmax[b], 0, s);
     if (e != cudaSuccess) return OT_ERR_CUDA;
   }
   return OT_OK;

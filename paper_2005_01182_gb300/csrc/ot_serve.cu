@@ -299,8 +299,9 @@ extern "C" {
 int ot_assign_submit(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int32_t m, int32_t algo,
                      uint64_t* ticket) {
   if (!ctx || !ticket) return OT_ERR_ARG;
-  if ((algo != OT_KM && algo != OT_BKM) || n <= 0 || m < n || !C || ldc < m)
+  if ((algo != OT_KM && algo != OT_BKM && algo != OT_AUTO) || n <= 0 || m < n || !C || ldc < m)
     return ctx_fail(ctx, OT_ERR_ARG, "bad arguments");
+  algo = resolve_algo(ctx, algo, m);
   ServeState* s = ctx->serve;
   cudaSetDevice(ctx->device);
   Layout L(n, m);

@@ -31,6 +31,7 @@ OT_ERR_UNSUPPORTED = -7
 OT_ERR_TICKET = -8
 OT_KM = 0
 OT_BKM = 1
+OT_AUTO = 2
 
 _lib = None
 

@@ -306,3 +306,29 @@ def test_autotune_keeps_results(oracle_mod, ctx):
             C = Cs[t]
             r, u, v = (x.cpu().numpy() for x in a.outs[t])
             assert oracle_mod.check_certificate(C, r, u, v, int(a.cost[t])) == 0
+
+
+def test_auto_algorithm_per_bucket(oracle_mod, ctx):
+    """OT_AUTO resolves per size bucket to KM or batched KM (both exact)."""
+    Cs = _batch(120, 16, 700, 77)
+    dev = [torch.from_numpy(C).cuda() for C in Cs]
+    for choice in (ot.OT_KM, ot.OT_BKM):
+        for m in (32, 64, 128, 256, 512, 1024):
+            ot.ot_tune_set(ctx, ot.OT_AUTO, m, choice, 0)
+        a = ot.ot_assign_solve_batched(ctx, dev, ot.OT_AUTO)
+        torch.cuda.synchronize()
+        for t, C in enumerate(Cs):
+            r, u, v = (x.cpu().numpy() for x in a.outs[t])
+            if choice == ot.OT_KM:
+                a0, c0, u0, v0 = oracle_mod.km(C)
+                np.testing.assert_array_equal(r, a0)
+                np.testing.assert_array_equal(u, u0)
+            assert oracle_mod.check_certificate(C, r, u, v, int(a.cost[t])) == 0
+    ot.ot_autotune(ctx, dev, ot.OT_AUTO, repeats=1)
+    a = ot.ot_assign_solve_batched(ctx, dev, ot.OT_AUTO)
+    torch.cuda.synchronize()
+    for t, C in enumerate(Cs):
+        r, u, v = (x.cpu().numpy() for x in a.outs[t])
+        assert oracle_mod.check_certificate(C, r, u, v, int(a.cost[t])) == 0
+    for m in (32, 64, 128, 256, 512, 1024):
+        ot.ot_tune_set(ctx, ot.OT_AUTO, m, ot.OT_KM if m <= 256 else ot.OT_BKM, 0)
