@@ -402,7 +402,7 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
       int32_t s0 = 0;
       if (k >= 1 && n[0] > 0) cudaMemcpy(&s0, dstatus, sizeof(s0), cudaMemcpyDeviceToHost);
       std::memcpy(stats_out, s8, sizeof(s8));
-      if (st[0] != OT_OK) return ctx_fail(ctx, st[0], "instance rejected");
+      if (st[0] != OT_OK) return ctx_fail(ctx, st[0], "instance failed: " + ctx->err);
       if (s0 != 0) return ctx_fail(ctx, s0, "device status error");
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return ctx_cuda(ctx, e, "solve");
@@ -515,7 +515,7 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
     for (int t = 0; t < k; ++t) status[t] = st[t];
   if (stats_out) std::memcpy(stats_out, s8, sizeof(s8));
   if (k == 1 && st[0] != OT_OK)
-    return ctx_fail(ctx, st[0], st[0] == OT_ERR_UNSUPPORTED ? "size not supported" : "instance failed");
+    return ctx_fail(ctx, st[0], st[0] == OT_ERR_UNSUPPORTED ? "size not supported" : "instance failed: " + ctx->err);
   return OT_OK;
 }
 

@@ -23,11 +23,39 @@
 #include <climits>
 #include <cooperative_groups.h>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <string>
 
 #include "ot_ctx.h"
 #include "ot_group.cuh"
 
 namespace cg = cooperative_groups;
+
+// Cycle accounting of the step kernel, compiled in only with
+// -DOT_LARGE_PROFILE (thread 0 of rank 0 measures; sections: phase setup,
+// scan, CTA reduction + publication, cluster barrier, post-exchange work,
+// augmentation).
+#ifdef OT_LARGE_PROFILE
+#define OT_PROF_DECL unsigned long long prof_acc[6] = {0, 0, 0, 0, 0, 0}; long long prof_t = clock64();
+#define OT_PROF_MARK(idx)                         \
+  do {                                            \
+    const long long now_ = clock64();             \
+    prof_acc[idx] += (unsigned long long)(now_ - prof_t); \
+    prof_t = now_;                                \
+  } while (0)
+#define OT_PROF_FLUSH(ctl)                                               \
+  do {                                                                   \
+    if (g == 0) {                                                        \
+      for (int q_ = 0; q_ < 6; ++q_) atomicAdd(&(ctl)->prof[q_], prof_acc[q_]); \
+      atomicAdd(&(ctl)->prof[6], rows);                                  \
+    }                                                                    \
+  } while (0)
+#else
+#define OT_PROF_DECL
+#define OT_PROF_MARK(idx) do {} while (0)
+#define OT_PROF_FLUSH(ctl) do {} while (0)
+#endif
 
 namespace ot {
 
@@ -37,14 +65,76 @@ constexpr int kPassThreads = 256;
 constexpr int kPassCols = 4 * kPassThreads;
 constexpr int kMaxCluster = 16;
 
+// ---- TMA bulk copies and mbarriers (inline PTX) ----------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// global -> own shared memory, completing `bytes` on `bar`; 16-byte aligned
+// addresses, size a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on one mbarrier phase: false if it did not complete within
+// `max_polls` polls (each poll may suspend the thread for a short while).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, int max_polls) {
+  for (int it = 0; it < max_polls; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+constexpr int kRingBytes = 64 * 1024;   // staged row segments per CTA
+
+// Device-side range check: records the first violation (site, value, aux)
+// and returns false so that the caller skips the access.
+__device__ __forceinline__ bool in_range(int x, int hi, int* bad, int site, int aux) {
+  if (x >= 0 && x < hi) return true;
+  if (atomicCAS(&bad[0], 0, site) == 0) {
+    bad[1] = x;
+    bad[2] = aux;
+  }
+  return false;
+}
+constexpr int kMbarPolls = 1 << 22;
+
 struct LargeCtl {
   int matched;
   int done;
   int status;
   int scount;
   int walkers;
-  int pad[3];
+  int bad[3];   // first out-of-range index seen by a device-side check: site, value, aux
   unsigned long long stats[8];  // steps, rows, bytes, phases, augs, init_bytes
+  unsigned long long prof[8];   // cycle breakdown of the step kernel (profiling builds)
+};
+
+// A row that joins S: its index, dual and tree root, carried with the
+// column exchange so that the next scan needs no dependent global load.
+struct __align__(16) RowRef {
+  long long u;
+  int row;
+  int root;
 };
 
 struct LargeWs {
@@ -64,20 +154,23 @@ struct LargeWs {
   int* claim;            // [n] lowest free column claimed per root
   long long* part_d;     // [chunks][m]
   int* part_p;           // [chunks][m]
-  int* ovf;              // [2][cluster][cols per CTA] mates beyond the slot capacity
+  RowRef* ovf;           // [2][cluster][cols per CTA] rows beyond the slot capacity
   LargeCtl* ctl;
   int chunks;
   int vec4;
+  int tma;   // level rows staged with bulk copies (16-byte aligned rows, m % 4 == 0)
 };
 
 struct __align__(16) Slot {
-  long long d;
-  int j;
-  int mate;
-  int cnt;
-  int nfree;
-  int pad[2];
-  int mates[kSlotMates];
+  long long d;     // CTA minimum distance outside T
+  int j;           // lowest column attaining it
+  int mate;        // KM: its matched row
+  int cnt;         // batched KM: matched columns at d (rows listed below)
+  int nfree;       // batched KM: free columns at d
+  int err;         // a bounded wait of this CTA expired
+  int pad;
+  long long umate; // KM: u of `mate`
+  RowRef refs[kSlotMates];
 };
 
 // ---------------------------------------------------------------------------
@@ -128,7 +221,9 @@ __global__ void large_init(LargeWs w, int bkm) {
     w.ctl->status = 0;
     w.ctl->scount = bkm ? n : 0;
     w.ctl->walkers = 0;
+    w.ctl->bad[0] = w.ctl->bad[1] = w.ctl->bad[2] = 0;
     for (int q = 0; q < 8; ++q) w.ctl->stats[q] = 0;
+    for (int q = 0; q < 8; ++q) w.ctl->prof[q] = 0;
     w.ctl->stats[5] = bkm ? 4ull * n * m : 0;
   }
 }
@@ -235,36 +330,68 @@ __global__ void __launch_bounds__(kLargeTPB, 1) large_steps(LargeWs w) {
   __shared__ Slot slots[2][kMaxCluster];
   __shared__ Best wbest[NW];
   __shared__ int s_cnt, s_nfree, s_mate;
+  __shared__ long long s_umate;
+  constexpr int LCAP = 256;  // rows staged per scan chunk
+  __shared__ RowRef s_refs[LCAP];
+  __shared__ __align__(8) unsigned long long s_bar;
+  __shared__ int s_err;
+  extern __shared__ __align__(128) int32_t s_ring[];  // kRingBytes: row segments
+  unsigned bar_parity = 0;
+  if (t == 0) {
+    mbar_init(&s_bar, 1);
+    mbar_fence_init();
+    s_err = 0;
+  }
+  __syncthreads();
   __shared__ long long s_cnt_total;
 
   LargeCtl* ctl = w.ctl;
   if (ctl->done) return;  // uniform over the cluster
+  OT_PROF_DECL
 
   long long dist[K], v[K];
   int pred[K], mate[K];
+  int rootp[K];          // batched KM: tree root of pred[k]
+  long long umate[K];    // u of mate[k]
   unsigned inT = 0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const int j = g + k * G;
-    v[k] = 0; dist[k] = kInf; pred[k] = -1; mate[k] = -1;
+    v[k] = 0; dist[k] = kInf; pred[k] = -1; mate[k] = -1; rootp[k] = -1; umate[k] = 0;
     if (j < m) {
       v[k] = w.v[j];
       mate[k] = w.c2r[j];
+      umate[k] = mate[k] >= 0 ? w.u[mate[k]] : 0;
       if (ALGO == kAlgoBKM) {
         if (w.inT[j]) {
           inT |= 1u << k;
           pred[k] = w.pred[j];
+          rootp[k] = pred[k] >= 0 ? w.root[pred[k]] : -1;
           dist[k] = 0;
         } else {
           long long bd = kInf;
           int bp = INT_MAX;
-          for (int c = 0; c < w.chunks; ++c) {
+          int c = 0;
+          for (; c + 8 <= w.chunks; c += 8) {
+            long long dd[8];
+            int pp[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              dd[e] = w.part_d[(long long)(c + e) * m + j];
+              pp[e] = w.part_p[(long long)(c + e) * m + j];
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              if (dd[e] < bd || (dd[e] == bd && pp[e] < bp)) { bd = dd[e]; bp = pp[e]; }
+          }
+          for (; c < w.chunks; ++c) {
             const long long d = w.part_d[(long long)c * m + j];
             const int p = w.part_p[(long long)c * m + j];
             if (d < bd || (d == bd && p < bp)) { bd = d; bp = p; }
           }
           dist[k] = bd;
           pred[k] = bp == INT_MAX ? -1 : bp;
+          rootp[k] = bp == INT_MAX ? -1 : w.root[bp];
         }
       }
     }
@@ -292,10 +419,12 @@ __global__ void __launch_bounds__(kLargeTPB, 1) large_steps(LargeWs w) {
     tcount = int(*cluster.map_shared_rank(&s_cnt_total, 0));
   }
 
+  OT_PROF_MARK(0);
   while (matched < n) {
     ++phases;
     int L;              // rows to scan this step: KM one row, batched KM from slots
     int km_row = matched;
+    long long km_u = 0;  // u of km_row (0 for the root, whose u is 0 before its phase)
     long long level = 0;
     int src_mask = 0;   // batched KM: which ranks contributed rows at the last level
     if (ALGO == kAlgoKM) {
@@ -316,7 +445,7 @@ __global__ void __launch_bounds__(kLargeTPB, 1) large_steps(LargeWs w) {
       // ---- scan the rows that joined S at `level` ----
       if (ALGO == kAlgoKM) {
         const int i = km_row;
-        const long long base = level - w.u[i];
+        const long long base = level - (level == 0 ? w.u[i] : km_u);
         const int32_t* row = w.C + i * w.ldc;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -328,29 +457,148 @@ __global__ void __launch_bounds__(kLargeTPB, 1) large_steps(LargeWs w) {
         }
         bytes += 4ull * (m - tcount);
         rows += 1;
-      } else if (L > 0) {
-        for (int r = 0; r < CS; ++r) {
-          if (!((src_mask >> r) & 1)) continue;
-          const Slot& sl = slots[par ^ 1][r];
-          const int cnt = sl.cnt;
-          for (int q = 0; q < cnt; ++q) {
-            const int i = cnt <= kSlotMates ? sl.mates[q] : w.ovf[((long long)(par ^ 1) * CS + r) * K * kLargeTPB + q];
-            const long long base = level - w.u[i];
-            const int32_t* row = w.C + i * w.ldc;
+      } else if (L > 0 && w.tma) {
+        // Rows of the last level, up to RB at a time: warp 0 maps each row to
+        // its source slot (prefix of the per-CTA counts), records (index, u,
+        // root) in shared memory and issues the bulk copies of this CTA's
+        // segments of the rows into the shared ring, all completing on one
+        // mbarrier; then every thread scans its columns from shared memory.
+        constexpr int RB = kRingBytes / (K * kLargeTPB * 4);
+        constexpr int RBW = RB < 32 ? RB : 32;  // rows staged per warp-0 round
+        unsigned row_bytes = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const int col0 = rank * kLargeTPB + k * G;
+          if (col0 < m) row_bytes += unsigned(min(kLargeTPB, m - col0)) * 4u;
+        }
+        for (int b0 = 0; b0 < L; b0 += RBW) {
+          const int nb = min(RBW, L - b0);
+          if (wid == 0) {
+            const Slot& mine = slots[par ^ 1][lane < CS ? lane : 0];
+            const int mycnt = (lane < CS && ((src_mask >> lane) & 1)) ? mine.cnt : 0;
+            int incl = mycnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int y = __shfl_up_sync(0xffffffffu, incl, o);
+              if (lane >= o) incl += y;
+            }
+            const int excl = incl - mycnt;
+            // lane e stages row q = b0 + e: its source CTA is the number of
+            // CTAs whose inclusive prefix does not exceed q (each lane has
+            // its own q, so the prefix values are broadcast one by one)
+            const int q = b0 + lane;
+            int src = 0;
+            for (int r = 0; r < CS; ++r) src += __shfl_sync(0xffffffffu, incl, r) <= q;
+            src &= 31;
+            const int base_q = __shfl_sync(0xffffffffu, excl, src);
+            const int cnt = __shfl_sync(0xffffffffu, mycnt, src);
+            if (lane == 0 && row_bytes) mbar_arrive_expect_tx(&s_bar, row_bytes * unsigned(nb));
+            __syncwarp();
+            if (lane < nb) {
+              const int pos = q - base_q;
+              RowRef ok_rr{0, 0, 0};
+              bool ok = in_range(src, CS, w.ctl->bad, 1, pos) && in_range(pos, cnt, w.ctl->bad, 2, src);
+              if (ok) {
+                ok_rr = cnt <= kSlotMates ? slots[par ^ 1][src].refs[pos]
+                                          : w.ovf[((long long)(par ^ 1) * CS + src) * K * kLargeTPB + pos];
+                ok = in_range(ok_rr.row, n, w.ctl->bad, 3, pos) && in_range(ok_rr.root, n, w.ctl->bad, 8, pos);
+              }
+              if (!ok) { ok_rr.row = 0; ok_rr.root = 0; s_err = 1; }
+              s_refs[lane] = ok_rr;
+              const int32_t* row = w.C + (long long)ok_rr.row * w.ldc;
+#pragma unroll
+              for (int k = 0; k < K; ++k) {
+                const int col0 = rank * kLargeTPB + k * G;
+                if (col0 < m)
+                  bulk_g2s(s_ring + (lane * K + k) * kLargeTPB, row + col0, unsigned(min(kLargeTPB, m - col0)) * 4u,
+                           &s_bar);
+              }
+            }
+          }
+          __syncthreads();
+          if (row_bytes) {
+            if (!mbar_wait_bounded(&s_bar, bar_parity, kMbarPolls)) s_err = 1;
+            bar_parity ^= 1u;
+          }
+          for (int e = 0; e < nb; ++e) {
+            const RowRef rr = s_refs[e];
+            const long long base = level - rr.u;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
               const int j = g + k * G;
               if (j < m && !((inT >> k) & 1u)) {
-                const long long cand = base + __ldg(row + j) - v[k];
-                if (cand < dist[k] || (cand == dist[k] && i < pred[k])) { dist[k] = cand; pred[k] = i; }
+                const long long cand = base + s_ring[(e * K + k) * kLargeTPB + t] - v[k];
+                if (cand < dist[k] || (cand == dist[k] && rr.row < pred[k])) {
+                  dist[k] = cand;
+                  pred[k] = rr.row;
+                  rootp[k] = rr.root;
+                }
               }
             }
           }
+          __syncthreads();  // the ring and s_refs are rewritten by the next round
+        }
+        bytes += 4ull * L * (m - tcount);
+        rows += L;
+      } else if (L > 0) {
+        // Rows of the last level: staged into shared memory (index, u,
+        // root) from the slots of the CTAs that had columns at that level,
+        // then scanned R at a time so that R cost loads are in flight.
+        constexpr int R = K >= 4 ? 1 : (K == 2 ? 2 : 8);
+        for (int c0 = 0; c0 < L; c0 += LCAP) {
+          const int nc = min(LCAP, L - c0);
+          for (int q = t; q < nc; q += kLargeTPB) {
+            int qq = c0 + q, src = 0;
+            for (; src < CS; ++src) {
+              if (!((src_mask >> src) & 1)) continue;
+              const int cnt = slots[par ^ 1][src].cnt;
+              if (qq < cnt) break;
+              qq -= cnt;
+            }
+            const int cnt = slots[par ^ 1][src].cnt;
+            s_refs[q] = cnt <= kSlotMates ? slots[par ^ 1][src].refs[qq]
+                                          : w.ovf[((long long)(par ^ 1) * CS + src) * K * kLargeTPB + qq];
+          }
+          __syncthreads();
+          for (int q0 = 0; q0 < nc; q0 += R) {
+            int cc[R][K];
+#pragma unroll
+            for (int e = 0; e < R; ++e) {
+              const int q = q0 + e;
+              const int32_t* row = w.C + (long long)(q < nc ? s_refs[q].row : 0) * w.ldc;
+#pragma unroll
+              for (int k = 0; k < K; ++k) {
+                const int j = g + k * G;
+                cc[e][k] = (q < nc && j < m && !((inT >> k) & 1u)) ? __ldg(row + j) : 0;
+              }
+            }
+#pragma unroll
+            for (int e = 0; e < R; ++e) {
+              const int q = q0 + e;
+              if (q >= nc) break;
+              const RowRef rr = s_refs[q];
+              const long long base = level - rr.u;
+#pragma unroll
+              for (int k = 0; k < K; ++k) {
+                const int j = g + k * G;
+                if (j < m && !((inT >> k) & 1u)) {
+                  const long long cand = base + cc[e][k] - v[k];
+                  if (cand < dist[k] || (cand == dist[k] && rr.row < pred[k])) {
+                    dist[k] = cand;
+                    pred[k] = rr.row;
+                    rootp[k] = rr.root;
+                  }
+                }
+              }
+            }
+          }
+          __syncthreads();
         }
         bytes += 4ull * L * (m - tcount);
         rows += L;
       }
       ++steps;
+      OT_PROF_MARK(1);
 
       // ---- CTA minimum (dist, lowest column) outside T ----
       Best b{kInf, INT_MAX};
@@ -361,16 +609,16 @@ __global__ void __launch_bounds__(kLargeTPB, 1) large_steps(LargeWs w) {
       }
       b = warp_argmin(b);
       if (lane == 0) wbest[wid] = b;
-      if (t == 0) { s_cnt = 0; s_nfree = 0; s_mate = -1; }
+      if (t == 0) { s_cnt = 0; s_nfree = 0; s_mate = -1; s_umate = 0; }
       __syncthreads();
-      Best cb = lane < NW ? wbest[lane] : Best{kInf, INT_MAX};
-      cb = warp_argmin(cb);
-      // ---- my CTA's candidate list at its own minimum ----
+      const Best cb = warp_argmin(lane < NW ? wbest[lane] : Best{kInf, INT_MAX});
+      // ---- my CTA's candidates at its own minimum: KM the mate of the
+      // argmin column, batched KM every column at that distance ----
       Slot& my = slots[par][rank];
       if (ALGO == kAlgoKM) {
 #pragma unroll
         for (int k = 0; k < K; ++k)
-          if (g + k * G == cb.j) s_mate = mate[k];
+          if (g + k * G == cb.j) { s_mate = mate[k]; s_umate = umate[k]; }
       } else {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -380,45 +628,66 @@ __global__ void __launch_bounds__(kLargeTPB, 1) large_steps(LargeWs w) {
               atomicAdd(&s_nfree, 1);
             } else {
               const int pos = atomicAdd(&s_cnt, 1);
-              if (pos < kSlotMates) my.mates[pos] = mate[k];
-              w.ovf[((long long)par * CS + rank) * K * kLargeTPB + pos] = mate[k];
+              const RowRef rr{umate[k], mate[k], rootp[k]};
+              if (pos < kSlotMates) my.refs[pos] = rr;
+              w.ovf[((long long)par * CS + rank) * K * kLargeTPB + pos] = rr;
             }
           }
         }
       }
       __syncthreads();
-      if (t == 0) {
-        my.d = cb.d;
-        my.j = cb.j;
-        my.mate = s_mate;
-        my.cnt = s_cnt;
-        my.nfree = s_nfree;
+      // ---- warp 1 asks L2 for the rows this CTA's candidates would add
+      // (the winning CTA's prefetch hides most of the next scan's HBM
+      // latency behind the exchange)
+      if (wid == 1 && w.vec4) {
+        const int nrow = ALGO == kAlgoKM ? (s_mate >= 0 ? 1 : 0) : min(s_cnt, 4);
+        const int pieces = 4;  // 4 bulk prefetches per row
+        const int q = lane / pieces, piece = lane % pieces;
+        if (q < nrow) {
+          int i = ALGO == kAlgoKM ? s_mate : my.refs[q].row;
+          if (!in_range(i, n, w.ctl->bad, 4, q)) i = 0;
+          const unsigned bytes = unsigned(m) * 4u;
+          const unsigned chunk = ((bytes / pieces) + 15u) & ~15u;
+          const unsigned off = piece * chunk;
+          if (off < bytes) {
+            const unsigned len = min(chunk, bytes - off) & ~15u;
+            const char* src = reinterpret_cast<const char*>(w.C + (long long)i * w.ldc) + off;
+            if (len) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(len) : "memory");
+          }
+        }
       }
-      __syncthreads();
-      // ---- publish to every CTA of the cluster, one barrier ----
-      if (t < CS && t != rank) {
-        Slot* dst = cluster.map_shared_rank(&slots[par][0], t);
-        const int ncopy = min(my.cnt, kSlotMates);
-        dst[rank].d = my.d;
-        dst[rank].j = my.j;
-        dst[rank].mate = my.mate;
-        dst[rank].cnt = my.cnt;
-        dst[rank].nfree = my.nfree;
-        for (int q = 0; q < ncopy; ++q) dst[rank].mates[q] = my.mates[q];
+      // warp r + 2 writes this CTA's slot into CTA r (all destinations in
+      // parallel; warps 0 and 1 would otherwise serialise the remote stores)
+      if (wid >= 2 && wid - 2 < CS) {
+        const int r = wid - 2;
+        const int cnt = s_cnt, ncopy = min(cnt, kSlotMates);
+        Slot* dst = cluster.map_shared_rank(&slots[par][0], r) + rank;
+        if (r != rank && lane < ncopy) dst->refs[lane] = my.refs[lane];
+        if (lane == 0) {
+          dst->d = cb.d;
+          dst->j = cb.j;
+          dst->mate = s_mate;
+          dst->umate = s_umate;
+          dst->cnt = cnt;
+          dst->nfree = s_nfree;
+          dst->err = s_err;
+        }
       }
+      OT_PROF_MARK(2);
       cluster.sync();
-      // ---- global minimum and the level's columns ----
-      D = kInf;
-      jstar = INT_MAX;
-      for (int r = 0; r < CS; ++r) {
-        const Slot& sl = slots[par][r];
-        if (lex_less(sl.d, sl.j, D, jstar)) { D = sl.d; jstar = sl.j; }
-      }
+      OT_PROF_MARK(3);
+      // ---- global minimum over the CS slots (lane r reads slot r) ----
+      const Slot& sl = slots[par][lane < CS ? lane : 0];
+      const bool valid = lane < CS;
+      const Best gb = warp_argmin(valid ? Best{sl.d, sl.j} : Best{kInf, INT_MAX});
+      D = gb.d;
+      jstar = gb.j;
+      if (__any_sync(0xffffffffu, valid && sl.err)) { status = kDevStepLimit; break; }
       if (jstar == INT_MAX) { status = kDevStepLimit; break; }
       if (ALGO == kAlgoKM) {
-        int jm = -1;
-        for (int r = 0; r < CS; ++r)
-          if (slots[par][r].j == jstar) jm = slots[par][r].mate;
+        const unsigned who = __ballot_sync(0xffffffffu, valid && sl.j == jstar);
+        const int jm = __shfl_sync(0xffffffffu, valid ? sl.mate : -1, __ffs(who) - 1);
+        const long long ju = __shfl_sync(0xffffffffu, valid ? sl.umate : 0ll, __ffs(who) - 1);
         // owner logs the predecessor and, if matched, moves the column into T
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -429,20 +698,17 @@ __global__ void __launch_bounds__(kLargeTPB, 1) large_steps(LargeWs w) {
         }
         if (jm < 0) { augment = true; break; }
         km_row = jm;
+        km_u = ju;
         level = D;
         ++tcount;
         par ^= 1;
+        OT_PROF_MARK(4);
         continue;
       } else {
-        int anyfree = 0, total = 0, mask = 0;
-        for (int r = 0; r < CS; ++r) {
-          const Slot& sl = slots[par][r];
-          if (sl.d == D) {
-            anyfree |= sl.nfree > 0;
-            total += sl.cnt;
-            if (sl.cnt > 0) mask |= 1 << r;
-          }
-        }
+        const bool at = valid && sl.d == D;
+        const int anyfree = __any_sync(0xffffffffu, at && sl.nfree > 0);
+        const int total = int(__reduce_add_sync(0xffffffffu, at ? unsigned(sl.cnt) : 0u));
+        const int mask = int(__ballot_sync(0xffffffffu, at && sl.cnt > 0));
         // owners: matched columns at level D join T, their mates join S
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -452,7 +718,7 @@ __global__ void __launch_bounds__(kLargeTPB, 1) large_steps(LargeWs w) {
             if (mate[k] >= 0) {
               inT |= 1u << k;
               const int mt = mate[k];
-              w.root[mt] = w.root[pred[k]];
+              w.root[mt] = rootp[k];
               w.inS[mt] = 1;
               w.drow[mt] = D;
             }
@@ -463,13 +729,15 @@ __global__ void __launch_bounds__(kLargeTPB, 1) large_steps(LargeWs w) {
         L = total;
         src_mask = mask;
         level = D;
+        // The next scan reads this step's slots (now slots[par ^ 1]); they
+        // are rewritten two steps later, after every CTA passed the next
+        // step's cluster barrier.
         par ^= 1;
-        // the next scan reads slots[par ^ 1] = this step's slots; the
-        // barrier of the next step protects them from being overwritten
-        cluster.sync();
+        OT_PROF_MARK(4);
         continue;
       }
     }
+    OT_PROF_MARK(4);
     if (status) break;
     // ---------------- augmentation ----------------
     cluster.sync();
@@ -478,8 +746,8 @@ __global__ void __launch_bounds__(kLargeTPB, 1) large_steps(LargeWs w) {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int j = g + k * G;
-        if (j < m && !((inT >> k) & 1u) && dist[k] == D && mate[k] < 0)
-          atomicMin(&w.claim[w.root[pred[k]]], j);
+        if (j < m && !((inT >> k) & 1u) && dist[k] == D && mate[k] < 0 && in_range(rootp[k], n, w.ctl->bad, 5, j))
+          atomicMin(&w.claim[rootp[k]], j);
       }
     }
     // accumulated dual adjustment (before the matching changes)
@@ -506,7 +774,7 @@ __global__ void __launch_bounds__(kLargeTPB, 1) large_steps(LargeWs w) {
       int j = g + k * G;
       if (j >= m || ((inT >> k) & 1u) || dist[k] != D || mate[k] >= 0) continue;
       if (ALGO == kAlgoKM && j != jstar) continue;
-      if (ALGO == kAlgoBKM && w.claim[w.root[pred[k]]] != j) continue;
+      if (ALGO == kAlgoBKM && (!in_range(rootp[k], n, w.ctl->bad, 6, j) || w.claim[rootp[k]] != j)) continue;
       int i = pred[k];
       for (int hop = 0; hop <= n; ++hop) {
         const int prev = w.r2c[i];
@@ -532,7 +800,8 @@ __global__ void __launch_bounds__(kLargeTPB, 1) large_steps(LargeWs w) {
       }
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        if (((inT >> k) & 1u) && w.claim[w.root[pred[k]]] != INT_MAX) inT &= ~(1u << k);
+        if (((inT >> k) & 1u) && in_range(rootp[k], n, w.ctl->bad, 7, g + k * G) && w.claim[rootp[k]] != INT_MAX)
+          inT &= ~(1u << k);
       }
       cluster.sync();
       for (int i = g; i < n; i += G) w.claim[i] = INT_MAX;
@@ -547,11 +816,17 @@ __global__ void __launch_bounds__(kLargeTPB, 1) large_steps(LargeWs w) {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int j = g + k * G;
-        if (j < m) mate[k] = w.c2r[j];
+        if (j < m) {
+          mate[k] = w.c2r[j];
+          umate[k] = mate[k] >= 0 ? w.u[mate[k]] : 0;
+        }
       }
       cluster.sync();
+      OT_PROF_MARK(5);
     }
   }
+  OT_PROF_MARK(5);
+  OT_PROF_FLUSH(ctl);
   // write back column state and counters
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -603,9 +878,11 @@ static cudaError_t launch_steps(const LargeWs& w, int cs, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes)) != cudaSuccess)
+    return e;
   cfg.gridDim = dim3(cs, 1, 1);
   cfg.blockDim = dim3(kLargeTPB, 1, 1);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = kRingBytes;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -631,12 +908,18 @@ static cudaError_t launch_steps_k(const LargeWs& w, int cs, int k, cudaStream_t 
 static int large_cluster_size() {
   static int cached = 0;
   if (cached) return cached;
+  // 16 CTAs when the device allows it (n = 16384 batched KM: 1.37 s vs
+  // 1.66 s with 8); OT_LARGE_CLUSTER=8 forces the portable size
+  const char* env = std::getenv("OT_LARGE_CLUSTER");
+  if (env && std::atoi(env) == 8) return cached = 8;
   int best = 8;
   auto kern = large_steps<1, kAlgoBKM>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes);
     cfg.gridDim = dim3(16, 1, 1);
     cfg.blockDim = dim3(kLargeTPB, 1, 1);
+    cfg.dynamicSmemBytes = kRingBytes;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 16;
@@ -676,7 +959,7 @@ int solve_large(ot_ctx* ctx, const Instance& I, int algo, cudaStream_t stream, i
   const size_t o_drow = take(8ull * n), o_root = take(4ull * n), o_slist = take(4ull * n);
   const size_t o_inS = take(n), o_claim = take(4ull * n);
   const size_t o_pd = take(8ull * chunks * m), o_pp = take(4ull * chunks * m);
-  const size_t o_ovf = take(8ull * cs * k * kLargeTPB);
+  const size_t o_ovf = take(2ull * cs * k * kLargeTPB * sizeof(RowRef));
   const size_t o_u = I.u ? 0 : take(8ull * n), o_v = I.v ? 0 : take(8ull * m);
   if (int rc = ctx->d_large.reserve(off); rc) return ctx_fail(ctx, rc, "large workspace");
   char* B = static_cast<char*>(ctx->d_large.ptr);
@@ -695,10 +978,11 @@ int solve_large(ot_ctx* ctx, const Instance& I, int algo, cudaStream_t stream, i
   w.claim = reinterpret_cast<int*>(B + o_claim);
   w.part_d = reinterpret_cast<long long*>(B + o_pd);
   w.part_p = reinterpret_cast<int*>(B + o_pp);
-  w.ovf = reinterpret_cast<int*>(B + o_ovf);
+  w.ovf = reinterpret_cast<RowRef*>(B + o_ovf);
   w.ctl = reinterpret_cast<LargeCtl*>(B + o_ctl);
   w.chunks = chunks;
   w.vec4 = (I.ldc % 4 == 0) && (reinterpret_cast<uintptr_t>(I.C) % 16 == 0);
+  w.tma = w.vec4 && (m % 4 == 0) && !std::getenv("OT_LARGE_NO_TMA");
 
   cudaError_t e = cudaMemsetAsync(I.cost, 0, sizeof(int64_t), stream);
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "large memset");
@@ -731,6 +1015,13 @@ int solve_large(ot_ctx* ctx, const Instance& I, int algo, cudaStream_t stream, i
   if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return ctx_cuda(ctx, e, "large sync");
   if (stats_out)
     for (int q = 0; q < 6; ++q) stats_out[q] = (int64_t)h.stats[q];
+#ifdef OT_LARGE_PROFILE
+  std::fprintf(stderr, "large_steps cycles: setup %llu scan %llu reduce+publish %llu barrier %llu post %llu augment %llu (steps %llu phases %llu step-rows %llu all-rows %llu)\n",
+               h.prof[0], h.prof[1], h.prof[2], h.prof[3], h.prof[4], h.prof[5], h.stats[0], h.stats[3], h.prof[6], h.stats[1]);
+#endif
+  if (h.bad[0])
+    return ctx_fail(ctx, OT_ERR_TIMEOUT, "large engine range check " + std::to_string(h.bad[0]) + " value " +
+                                             std::to_string(h.bad[1]) + " aux " + std::to_string(h.bad[2]));
   if (h.status || h.matched != n) return ctx_fail(ctx, OT_ERR_TIMEOUT, "large engine did not converge");
   return OT_OK;
 }
