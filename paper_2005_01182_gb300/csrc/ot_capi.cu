@@ -165,7 +165,7 @@ struct Bucket {
 // launched.  Writes per-instance stats into ctx->d_stats (k x 8).
 int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts,
                      const std::vector<int>& skip, int algo, cudaStream_t stream, bool fork,
-                     bool own_stats, std::vector<int>* unsupported) {
+                     bool own_stats, std::vector<int>* unsupported, bool allow_cluster) {
   const int k = int(insts.size());
   if (own_stats) {
     if (int rc = slot.d_stats.reserve(size_t(k) * 8 * sizeof(int64_t)); rc) return ctx_fail(ctx, rc, "stats alloc");
@@ -173,6 +173,13 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
     for (int t = 0; t < k; ++t) insts[t].stats = dstats + size_t(t) * 8;
   }
 
+  // A handful of wide batched-KM instances solve faster on the cluster
+  // engine (16 SMs and grid-wide passes each) than one CTA apiece; many of
+  // them keep the group engine busy on every SM.
+  int wide_bkm = 0;
+  for (int t = 0; t < k; ++t)
+    if (!skip[t] && insts[t].m > kClusterRouteCols && resolve_algo(ctx, algo, insts[t].m) == kAlgoBKM) ++wide_bkm;
+  const bool route_wide = allow_cluster && wide_bkm > 0 && wide_bkm <= kClusterRouteMax;
   // bucket by (algorithm, tuned shape)
   std::map<int, Bucket> buckets;
   for (int t = 0; t < k; ++t) {
@@ -180,6 +187,7 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
     const Instance& I = insts[t];
     const int ia = resolve_algo(ctx, algo, I.m);
     int sh = ctx->table[ia][bucket_of(I.m)];
+    if (route_wide && ia == kAlgoBKM && I.m > kClusterRouteCols && !ctx->tuned[ia][bucket_of(I.m)]) sh = kLargeEngine;
     if (sh == kLargeEngine) {  // bucket routed to the cluster engine
       if (unsupported) unsupported->push_back(t);
       continue;
@@ -363,7 +371,7 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
       if (n[t] == 0 && st[t] == OT_OK) skip[t] = 1;  // handled below
     }
     std::vector<int> unsup;
-    if (int rc = run_device_batch(ctx, ctx->api, insts, skip, algo, stream, true, true, &unsup); rc) return rc;
+    if (int rc = run_device_batch(ctx, ctx->api, insts, skip, algo, stream, true, true, &unsup, true); rc) return rc;
     ctx->last_k = k;
     ctx->last_skip = skip;
     // instances wider than a group: the cluster engine, one at a time
@@ -469,7 +477,7 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
     if (e != cudaSuccess) return ctx_cuda(ctx, e, "H2D");
   }
   std::vector<int> unsup;
-  if (int rc = run_device_batch(ctx, ctx->api, insts, skip, algo, stream, true, true, &unsup); rc) return rc;
+  if (int rc = run_device_batch(ctx, ctx->api, insts, skip, algo, stream, true, true, &unsup, true); rc) return rc;
   ctx->last_k = k;
   ctx->last_skip = skip;
   std::vector<int> still;
@@ -704,6 +712,7 @@ int ot_tune_set(ot_ctx* ctx, int32_t algo, int32_t m, int32_t tpi, int32_t k) {
   }
   if (tpi == 0 && k == 0) {  // route the bucket to the cluster engine
     ctx->table[algo][bucket_of(m)] = kLargeEngine;
+    ctx->tuned[algo][bucket_of(m)] = true;
     return OT_OK;
   }
   const int sh = shape_index(tpi, k);
@@ -711,6 +720,7 @@ int ot_tune_set(ot_ctx* ctx, int32_t algo, int32_t m, int32_t tpi, int32_t k) {
   if (sh < 0 || group_shape(sh).max_cols() < (32 << b) || m > kMaxGroupCols)
     return ctx_fail(ctx, OT_ERR_UNSUPPORTED, "shape not available for this bucket");
   ctx->table[algo][b] = sh;
+  ctx->tuned[algo][b] = true;
   return OT_OK;
 }
 
@@ -802,6 +812,7 @@ int ot_autotune(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* 
       }
       if (best >= 0) {
         ctx->table[a][kv.first] = best;
+        ctx->tuned[a][kv.first] = true;
         if (tf)
           std::fprintf(tf, "{\"algo\": %d, \"bucket_mmax\": %d, \"tpi\": %d, \"k\": %d, \"ms\": %.4f}\n",
                        a, 32 << kv.first, group_shape(best).tpi, group_shape(best).k, best_ms);
@@ -839,7 +850,10 @@ void load_tune_file(ot_ctx* ctx) {
     int au = -1;
     if ((p = std::strstr(line, "\"auto\":"))) au = std::atoi(p + 7);
     const int sh = shape_index(tpi, kk);
-    if ((a == 0 || a == 1) && mm > 0 && sh >= 0) ctx->table[a][bucket_of(mm)] = sh;
+    if ((a == 0 || a == 1) && mm > 0 && sh >= 0) {
+      ctx->table[a][bucket_of(mm)] = sh;
+      ctx->tuned[a][bucket_of(mm)] = true;
+    }
     if ((au == 0 || au == 1) && mm > 0) ctx->auto_algo[bucket_of(mm)] = au;
   }
   std::fclose(f);

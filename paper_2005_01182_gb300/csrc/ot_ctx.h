@@ -21,6 +21,10 @@ constexpr int kNumBuckets = 8;        // bucket b: m <= 32 << b
 constexpr int kMaxGroupCols = 4096;   // widest instance one group engine handles
 constexpr int kForkStreams = 4;
 constexpr int kLargeEngine = -2;  // table entry: use the cluster engine
+// At most this many batched-KM instances wider than kClusterRouteCols in one
+// call go to the cluster engine instead of a group each (API calls only).
+constexpr int kClusterRouteCols = 1024;
+constexpr int kClusterRouteMax = 4;
 int bucket_of(int m);
 int shape_index(int tpi, int k);
 void default_table(int table[2][kNumBuckets]);
@@ -72,6 +76,7 @@ struct ot_ctx {
   DevBuf d_status, d_io, d_scratch, d_large;
 
   int table[2][ot::kNumBuckets];
+  bool tuned[2][ot::kNumBuckets] = {};  // entry set by ot_tune_set / ot_autotune / tune file
   int auto_algo[ot::kNumBuckets];  // algorithm OT_AUTO resolves to, per bucket
   std::string tune_file;
 
@@ -87,12 +92,14 @@ bool ptr_on_device(const void* p);
 void load_tune_file(ot_ctx* ctx);
 // Bucket the instances by tuned group shape and launch them on `stream`
 // (forking buckets over the context's streams when `fork`).  Entries with
-// skip[t] set are not launched; instances no engine can take are listed in
-// *unsupported.  With `own_stats` the slot's stats block receives per-instance
-// counters, otherwise insts[t].stats is kept.
+// skip[t] set are not launched; instances the group engine does not take
+// (too wide, routed to the cluster engine, or -- with `allow_cluster` -- a
+// few wide batched-KM ones) are listed in *unsupported for the caller to
+// hand to the cluster engine.  With `own_stats` the slot's stats block
+// receives per-instance counters, otherwise insts[t].stats is kept.
 int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<ot::Instance>& insts,
                      const std::vector<int>& skip, int algo, cudaStream_t stream, bool fork,
-                     bool own_stats, std::vector<int>* unsupported);
+                     bool own_stats, std::vector<int>* unsupported, bool allow_cluster);
 // Wide-instance engine (ot_large.cu): one instance on a thread-block
 // cluster plus grid-wide passes; synchronises `stream`.
 int solve_large(ot_ctx* ctx, const ot::Instance& I, int algo, cudaStream_t stream, int64_t* stats_out);

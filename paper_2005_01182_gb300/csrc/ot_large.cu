@@ -312,6 +312,115 @@ __global__ void __launch_bounds__(kPassThreads) large_pass(LargeWs w) {
   if (blockIdx.x == 0 && threadIdx.x == 0 && r1 > r0) atomicAdd(&w.ctl->stats[1], (unsigned long long)(r1 - r0));
 }
 
+
+// ---------------------------------------------------------------------------
+// B2 pass, bulk-copy pipeline: the same result as large_pass, with the rows'
+// segments of this CTA's column tile (kTmaTileCols columns) streamed into a
+// shared-memory ring by cp.async.bulk, kTmaStages stages of kTmaRows rows in
+// flight, each stage completing on its own mbarrier.  Thread 0 produces,
+// every thread consumes 8 columns.  Needs 16-byte aligned rows, m % 4 == 0.
+// ---------------------------------------------------------------------------
+constexpr int kTmaTileCols = 8 * kPassThreads;                 // 2048 columns
+constexpr int kTmaRows = 4;                                   // rows per stage
+constexpr int kTmaStages = 3;
+constexpr int kTmaStageBytes = kTmaRows * kTmaTileCols * 4;   // 32 KB
+constexpr int kTmaPassSmem = kTmaStages * kTmaStageBytes;     // 96 KB
+
+__global__ void __launch_bounds__(kPassThreads) large_pass_tma(LargeWs w) {
+  if (w.ctl->done) return;
+  extern __shared__ __align__(128) int32_t ring[];
+  __shared__ __align__(8) unsigned long long bars[kTmaStages];
+  __shared__ int s_row[kTmaStages][kTmaRows];
+  __shared__ long long s_u[kTmaStages][kTmaRows];
+  const int m = w.m;
+  const int S = w.ctl->scount;
+  const int c = blockIdx.y;
+  const int r0 = int((long long)S * c / w.chunks), r1 = int((long long)S * (c + 1) / w.chunks);
+  const int tile0 = blockIdx.x * kTmaTileCols;
+  const int tcols = min(kTmaTileCols, m - tile0);           // multiple of 4
+  const unsigned seg_bytes = unsigned(tcols) * 4u;
+  const int t = threadIdx.x;
+  const int j0 = tile0 + 8 * t;
+  if (t == 0) {
+    for (int st = 0; st < kTmaStages; ++st) mbar_init(&bars[st], 1);
+    mbar_fence_init();
+  }
+  long long vj[8], bd[8];
+  int bp[8];
+  bool live[8];
+  int nlive = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int j = j0 + q;
+    live[q] = j < m && !w.inT[j];
+    vj[q] = j < m ? w.v[j] : 0;
+    bd[q] = kInf;
+    bp[q] = INT_MAX;
+    nlive += live[q];
+  }
+  __syncthreads();
+  const int nrows = r1 - r0;
+  const int nstages_total = (nrows + kTmaRows - 1) / kTmaRows;
+  // producer: fill stage st with rows [r0 + s*kTmaRows, ...)
+  auto produce = [&](int sidx) {
+    const int st = sidx % kTmaStages;
+    const int rb = r0 + sidx * kTmaRows;
+    const int nr = min(kTmaRows, r1 - rb);
+    for (int e = 0; e < nr; ++e) {
+      const int i = w.slist[rb + e];
+      s_row[st][e] = i;
+      s_u[st][e] = w.u[i];
+    }
+    mbar_arrive_expect_tx(&bars[st], seg_bytes * unsigned(nr));
+    for (int e = 0; e < nr; ++e)
+      bulk_g2s(ring + (st * kTmaRows + e) * kTmaTileCols, w.C + (long long)s_row[st][e] * w.ldc + tile0, seg_bytes,
+               &bars[st]);
+  };
+  if (t == 0)
+    for (int sidx = 0; sidx < min(kTmaStages, nstages_total); ++sidx) produce(sidx);
+  bool failed = false;
+  for (int sidx = 0; sidx < nstages_total; ++sidx) {
+    const int st = sidx % kTmaStages;
+    const unsigned parity = unsigned(sidx / kTmaStages) & 1u;
+    if (!mbar_wait_bounded(&bars[st], parity, kMbarPolls)) { failed = true; break; }
+    const int nr = min(kTmaRows, r1 - (r0 + sidx * kTmaRows));
+    for (int e = 0; e < nr; ++e) {
+      const int i = s_row[st][e];
+      const long long ui = s_u[st][e];
+      const int4* src = reinterpret_cast<const int4*>(ring + (st * kTmaRows + e) * kTmaTileCols + 8 * t);
+      const int4 a = src[0], b = src[1];
+      const int cv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const long long rc = (long long)cv[q] - ui - vj[q];
+        if (live[q] && (rc < bd[q] || (rc == bd[q] && i < bp[q]))) { bd[q] = rc; bp[q] = i; }
+      }
+    }
+    __syncthreads();  // stage st is free again
+    if (t == 0 && sidx + kTmaStages < nstages_total) produce(sidx + kTmaStages);
+  }
+  if (failed) {
+    // give copies still in flight a bounded chance to land before exiting
+    if (t == 0) {
+      w.ctl->status = kDevStepLimit;
+      for (int st = 0; st < kTmaStages; ++st) mbar_wait_bounded(&bars[st], 0, 1024);
+    }
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int j = j0 + q;
+    if (j < m) {
+      w.part_d[(long long)c * m + j] = bd[q];
+      w.part_p[(long long)c * m + j] = bp[q];
+    }
+  }
+  const long long wl = warp_sum((long long)nlive);
+  if ((threadIdx.x & 31) == 0 && wl > 0)
+    atomicAdd(&w.ctl->stats[2], (unsigned long long)(4 * wl * (r1 - r0)));
+  if (blockIdx.x == 0 && threadIdx.x == 0 && r1 > r0) atomicAdd(&w.ctl->stats[1], (unsigned long long)(r1 - r0));
+}
+
 // ---------------------------------------------------------------------------
 // cluster step engine
 // ---------------------------------------------------------------------------
@@ -992,12 +1101,27 @@ int solve_large(ot_ctx* ctx, const Instance& I, int algo, cudaStream_t stream, i
     if ((e = launch_steps_k<kAlgoKM>(w, cs, k, stream)) != cudaSuccess) return ctx_cuda(ctx, e, "large steps");
   } else {
     const dim3 pgrid(tiles, chunks, 1);
+    const int ttiles = (m + kTmaTileCols - 1) / kTmaTileCols;
+    const int tchunks = std::max(1, std::min((2 * sms + ttiles - 1) / ttiles, chunks));
+    const dim3 tgrid(ttiles, tchunks, 1);
+    const bool pass_tma = w.tma && !std::getenv("OT_PASS_NO_TMA");
+    if (pass_tma) {
+      w.chunks = tchunks;  // the step kernel reduces exactly the partials the pass writes
+      if ((e = cudaFuncSetAttribute(large_pass_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaPassSmem)) !=
+          cudaSuccess)
+        return ctx_cuda(ctx, e, "pass attribute");
+    }
     int batch = 4;
     LargeCtl h;
     for (int iter = 0; iter < 4 * n + 8; iter += batch) {
       for (int b = 0; b < batch; ++b) {
-        if (w.vec4) large_pass<1><<<pgrid, kPassThreads, 0, stream>>>(w);
-        else large_pass<0><<<pgrid, kPassThreads, 0, stream>>>(w);
+        if (pass_tma) {
+          large_pass_tma<<<tgrid, kPassThreads, kTmaPassSmem, stream>>>(w);
+        } else if (w.vec4) {
+          large_pass<1><<<pgrid, kPassThreads, 0, stream>>>(w);
+        } else {
+          large_pass<0><<<pgrid, kPassThreads, 0, stream>>>(w);
+        }
         if ((e = launch_steps_k<kAlgoBKM>(w, cs, k, stream)) != cudaSuccess) return ctx_cuda(ctx, e, "large steps");
       }
       if ((e = cudaMemcpyAsync(&h, w.ctl, sizeof(h), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)

@@ -220,7 +220,7 @@ void ServeState::launch_ready() {
     }
     if (insts.empty()) continue;
     std::vector<int> skip(insts.size(), 0), unsup;
-    int rc = run_device_batch(ctx, w->slot, insts, skip, algo, w->stream, false, false, &unsup);
+    int rc = run_device_batch(ctx, w->slot, insts, skip, algo, w->stream, false, false, &unsup, false);
     if (rc != OT_OK) {
       for (uint64_t t : ids) flags[reqs[t].flag] = rc;
     } else {

@@ -94,3 +94,28 @@ def test_single_16384(oracle_mod, ctx):
     a2, c2, u2, v2, _ = solve(ctx, C, ot.OT_KM)
     assert c2 == c
     assert oracle_mod.check_certificate(C, a2, u2, v2, c2) == 0
+
+
+def test_few_wide_batched_km_take_the_cluster_engine(oracle_mod):
+    """With an untuned table, a call with a handful of batched-KM instances
+    wider than 1024 columns runs them on the cluster engine (and many of
+    them on the group engine); both give certified optima."""
+    fresh = ot.Context()
+    try:
+        Cs = [W.uniform_costs(n, n + 3, seed=n) for n in (1100, 2047)]
+        dev = [torch.from_numpy(C).cuda() for C in Cs]
+        a = ot.ot_assign_solve_batched(fresh, dev, ot.OT_BKM)
+        torch.cuda.synchronize()
+        for t, C in enumerate(Cs):
+            r, u, v = (x.cpu().numpy() for x in a.outs[t])
+            c = int(a.cost[t])
+            assert oracle_mod.check_certificate(C, r, u, v, c) == 0
+            assert c == oracle_mod.km(C)[1]
+        many = [W.pixel_sqdist(1030 + 7 * i, seed=i) for i in range(6)]
+        a = ot.ot_assign_solve_batched(fresh, [torch.from_numpy(C).cuda() for C in many], ot.OT_BKM)
+        torch.cuda.synchronize()
+        for t, C in enumerate(many):
+            r, u, v = (x.cpu().numpy() for x in a.outs[t])
+            assert oracle_mod.check_certificate(C, r, u, v, int(a.cost[t])) == 0
+    finally:
+        fresh.close()
