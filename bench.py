@@ -98,8 +98,24 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def rank_seed(rank: int) -> int:
+    """Base seed of rank r's batch: every rank solves its own instances."""
+    return W.BASE_SEED + 1_000_003 * rank
+
+
 def batch_for_rank(rank: int, k: int):
-    return W.batch_embeddings(k, seed=W.BASE_SEED + 1_000_003 * rank)
+    return W.batch_embeddings(k, seed=rank_seed(rank))
+
+
+def job_throughput(local_ms: float, k: int, steps: int, world: int, dist=None, device=None) -> tuple[float, float]:
+    """Whole-job solves/s: every rank solved k instances per step; the job
+    took as long as the slowest rank (max over ranks of the timed region)."""
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return world * k * steps / (ms / 1000.0), ms
 
 
 def cpu_oracle_rate(Cs, budget_s: float):
@@ -137,6 +153,31 @@ def run_reference(args):
                              "sample": f"{per_step} instances per step of the 4096-instance batch, oracle KM, single thread"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def measure_single_4096(stream, ot, torch):
+    """n = m = 4096 single solves (circle/square shapes and uniform costs):
+    KM on one CTA vs batched KM (routed to the cluster engine), s/solve."""
+    out = {}
+    ctx = ot.Context()
+    for kind in ("circle-square", "uniform"):
+        Cd = torch.from_numpy(W.single_4096(kind)).cuda()
+        torch.cuda.synchronize()
+        res = {}
+        for name, algo in (("km", ot.OT_KM), ("batched_km", ot.OT_BKM)):
+            best = None
+            for _ in range(2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r, c, u, v, st = ot.ot_assign_solve_stats(ctx, Cd, algo, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1) / 1000.0
+                best = t if best is None else min(best, t)
+            res[name] = {"s_per_solve": best, "cost": int(c.item()), "steps": st["steps"]}
+        out[kind] = res
+    ctx.close()
+    return out
 
 
 def measure_single_16384(ctx, stream, ot, torch):
@@ -349,11 +390,7 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in evs]
     st = ot.ot_last_call_stats(ctx)
     launches_per_step = st["launches"]
-    tmax = torch.tensor([total_ms], device=dev)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    total_ms = float(tmax.item())
-    value = world * args.k * args.steps / (total_ms / 1000.0)
+    value, total_ms = job_throughput(total_ms, args.k, args.steps, world, dist if world > 1 else None, dev)
 
     # correctness spot check of the timed results (cost must be finite/status ok)
     assert (args_dev.status.cpu().numpy() == 0).all(), "device status error"
@@ -439,6 +476,7 @@ def main():
                                 "sample": f"first {done} instances of the batch, oracle KM single-threaded, {dt:.1f}s"}
         del Cs, dC, args_dev, args_host, hC, houts, slabC
         torch.cuda.empty_cache()
+        line["single_4096"] = measure_single_4096(stream, ot, torch)
         line["single_16384"] = measure_single_16384(ctx, stream, ot, torch)
         line["served"] = measure_served(ctx, stream, ot, torch, dev, args)
     elif rank == 0:
