@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <string>
@@ -154,6 +155,17 @@ static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 // cached CUDA graph)
 // ---------------------------------------------------------------------------
 
+// OT_GROUP_MAX_CTAS caps the persistent grid of batched launches
+// (experiments on how many instances should be in flight at once).
+static int max_ctas_env() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("OT_GROUP_MAX_CTAS");
+    v = e ? std::max(0, std::atoi(e)) : 0;
+  }
+  return v;
+}
+
 struct Bucket {
   int shape;
   int algo = 0;
@@ -263,7 +275,7 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
       for (auto& kv : buckets) {
         Bucket& b = kv.second;
         e = launch_group(group_shape(b.shape), b.algo, dinst, dorder + offs[bi], int(b.idx.size()),
-                         dwork + bi, b.nmax, b.mmax, 0, s);
+                         dwork + bi, b.nmax, b.mmax, max_ctas_env(), s);
         if (e != cudaSuccess) return e;
         ++bi;
       }
@@ -276,7 +288,7 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
       cudaStream_t bs = ctx->bstreams[bi % kForkStreams];
       if ((e = cudaStreamWaitEvent(bs, ctx->fork_ev, 0)) != cudaSuccess) return e;
       e = launch_group(group_shape(b.shape), b.algo, dinst, dorder + offs[bi], int(b.idx.size()),
-                       dwork + bi, b.nmax, b.mmax, 0, bs);
+                       dwork + bi, b.nmax, b.mmax, max_ctas_env(), bs);
       if (e != cudaSuccess) return e;
       ++bi;
     }

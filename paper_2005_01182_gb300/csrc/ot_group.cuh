@@ -246,42 +246,34 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
           }
         }
       } else {
-        // two rows per iteration so that their loads are in flight together
-        int q = 0;
-        for (; q + 2 <= L; q += 2) {
-          const int i0 = S.list[q], i1 = S.list[q + 1];
-          const long long b0 = level - S.u[i0], b1 = level - S.u[i1];
-          const int32_t* r0 = C + i0 * ldc;
-          const int32_t* r1 = C + i1 * ldc;
-          int c0[K], c1[K];
+        // R rows per round so that R x K cost loads are in flight together
+        // (1024-thread groups have 64 registers per thread: fewer rows)
+        constexpr int R = TPI >= 1024 ? (K >= 4 ? 2 : 4) : (K >= 8 ? 2 : (K >= 4 ? 4 : (K >= 2 ? 8 : 16)));
+        for (int q0 = 0; q0 < L; q0 += R) {
+          int cc[R][K];
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const int j = t + k * TPI;
-            const bool live = j < m && !((inT >> k) & 1u);
-            c0[k] = live ? __ldg(r0 + j) : 0;
-            c1[k] = live ? __ldg(r1 + j) : 0;
-          }
+          for (int e = 0; e < R; ++e) {
+            const int q = q0 + e;
+            const int32_t* row = C + (q < L ? S.list[q] : 0) * ldc;
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const int j = t + k * TPI;
-            if (j < m && !((inT >> k) & 1u)) {
-              const long long x0 = b0 + c0[k] - v[k];
-              if (x0 < dist[k] || (x0 == dist[k] && i0 < pred[k])) { dist[k] = x0; pred[k] = i0; }
-              const long long x1 = b1 + c1[k] - v[k];
-              if (x1 < dist[k] || (x1 == dist[k] && i1 < pred[k])) { dist[k] = x1; pred[k] = i1; }
+            for (int k = 0; k < K; ++k) {
+              const int j = t + k * TPI;
+              cc[e][k] = (q < L && j < m && !((inT >> k) & 1u)) ? __ldg(row + j) : 0;
             }
           }
-        }
-        for (; q < L; ++q) {
-          const int i = S.list[q];
-          const long long base = level - S.u[i];
-          const int32_t* row = C + i * ldc;
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const int j = t + k * TPI;
-            if (j < m && !((inT >> k) & 1u)) {
-              const long long cand = base + __ldg(row + j) - v[k];
-              if (cand < dist[k] || (cand == dist[k] && i < pred[k])) { dist[k] = cand; pred[k] = i; }
+          for (int e = 0; e < R; ++e) {
+            const int q = q0 + e;
+            if (q >= L) break;
+            const int i = S.list[q];
+            const long long base = level - S.u[i];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+              const int j = t + k * TPI;
+              if (j < m && !((inT >> k) & 1u)) {
+                const long long cand = base + cc[e][k] - v[k];
+                if (cand < dist[k] || (cand == dist[k] && i < pred[k])) { dist[k] = cand; pred[k] = i; }
+              }
             }
           }
         }
