@@ -221,6 +221,36 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
     b.mmax = std::max(b.mmax, I.m);
     b.idx.push_back(t);
   }
+  // 16-bit row packing for the group-engine instances (OT_PACK=0 disables)
+  static const bool pack_on = [] {
+    const char* e = std::getenv("OT_PACK");
+    return !(e && std::atoi(e) == 0);
+  }();
+  bool any_pack = false;
+  if (pack_on && !buckets.empty()) {
+    size_t nrows = 0, nelem = 0;
+    for (auto& kv : buckets)
+      for (int t : kv.second.idx) { nrows += insts[t].n; nelem += size_t(insts[t].n) * insts[t].m; }
+    const size_t b_pok = al256(sizeof(int32_t) * k), b_roff = al256(sizeof(int32_t) * nrows);
+    const int genp = slot.d_pack.generation;
+    if (slot.d_pack.reserve(b_pok + b_roff + al256(2 * nelem)) == OT_OK) {
+      if (slot.d_pack.generation != genp) slot.clear_graphs();
+      char* base = static_cast<char*>(slot.d_pack.ptr);
+      int32_t* pok = reinterpret_cast<int32_t*>(base);
+      int32_t* roff = reinterpret_cast<int32_t*>(base + b_pok);
+      uint16_t* P = reinterpret_cast<uint16_t*>(base + b_pok + b_roff);
+      size_t orow = 0, oel = 0;
+      for (auto& kv : buckets)
+        for (int t : kv.second.idx) {
+          insts[t].pok = pok + t;
+          insts[t].roff = roff + orow;
+          insts[t].P = P + oel;
+          orow += insts[t].n;
+          oel += size_t(insts[t].n) * insts[t].m;
+        }
+      any_pack = true;
+    }
+  }
   // a shape may serve several m-buckets; keep the smem bound feasible
   for (auto& kv : buckets) {
     Bucket& b = kv.second;
@@ -261,7 +291,7 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
     key += "|" + std::to_string(b.algo) + ":" + std::to_string(b.shape) + "," + std::to_string(b.idx.size()) + "," +
            std::to_string(b.nmax) + "," + std::to_string(b.mmax);
   }
-  key += "|" + std::to_string(reinterpret_cast<uintptr_t>(stream));
+  key += "|" + std::to_string(reinterpret_cast<uintptr_t>(stream)) + (any_pack ? "|p" : "");
 
   const Instance* dinst = reinterpret_cast<const Instance*>(d);
   const int32_t* dorder = reinterpret_cast<const int32_t*>(d + desc_bytes);
@@ -270,6 +300,7 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
   auto enqueue = [&](cudaStream_t s) -> cudaError_t {
     cudaError_t e = cudaMemcpyAsync(d, h, total, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
+    if (any_pack && (e = launch_pack(dinst, nullptr, k, s)) != cudaSuccess) return e;
     if (nb == 1 || !fork) {
       int bi = 0;
       for (auto& kv : buckets) {
@@ -341,10 +372,14 @@ static int check_sizes(const void* C, int64_t ldc, int n, int m) {
 }
 
 // Solve k instances; every pointer is either device (dev=true) or host.
+// route_wide: single-instance entry points let a wide batched-KM instance
+// take the cluster engine (the batched entry point keeps the group engine
+// unless the table says otherwise, so that its results do not depend on
+// how many wide instances a call carries).
 static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t* ldc,
                       const int32_t* n, const int32_t* m, int algo, int32_t* const* r2c,
                       int64_t* cost, int64_t* const* u, int64_t* const* v, int32_t* status,
-                      cudaStream_t stream, ot_stats* stats_out) {
+                      cudaStream_t stream, ot_stats* stats_out, bool route_wide) {
   if (algo != OT_KM && algo != OT_BKM && algo != OT_AUTO) return ctx_fail(ctx, OT_ERR_ARG, "bad algo");
   if (k < 0) return ctx_fail(ctx, OT_ERR_ARG, "k < 0");
   if (k == 0) return OT_OK;
@@ -383,7 +418,7 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
       if (n[t] == 0 && st[t] == OT_OK) skip[t] = 1;  // handled below
     }
     std::vector<int> unsup;
-    if (int rc = run_device_batch(ctx, ctx->api, insts, skip, algo, stream, true, true, &unsup, true); rc) return rc;
+    if (int rc = run_device_batch(ctx, ctx->api, insts, skip, algo, stream, true, true, &unsup, route_wide); rc) return rc;
     ctx->last_k = k;
     ctx->last_skip = skip;
     // instances wider than a group: the cluster engine, one at a time
@@ -489,7 +524,7 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
     if (e != cudaSuccess) return ctx_cuda(ctx, e, "H2D");
   }
   std::vector<int> unsup;
-  if (int rc = run_device_batch(ctx, ctx->api, insts, skip, algo, stream, true, true, &unsup, true); rc) return rc;
+  if (int rc = run_device_batch(ctx, ctx->api, insts, skip, algo, stream, true, true, &unsup, route_wide); rc) return rc;
   ctx->last_k = k;
   ctx->last_skip = skip;
   std::vector<int> still;
@@ -558,6 +593,7 @@ void LaunchSlot::release() {
   clear_graphs();
   d_meta.release();
   d_stats.release();
+  d_pack.release();
   h_meta.release();
   if (meta_ev) cudaEventDestroy(meta_ev);
   meta_ev = nullptr;
@@ -639,7 +675,7 @@ int ot_assign_solve(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int32
   // single device solves report their status when asked via *_stats
   const bool dev = n > 0 ? ptr_on_device(C) : ptr_on_device(cost);
   return solve_many(ctx, 1, Cs, ld, ns, ms, algo, rs, cost, u ? us : nullptr, v ? vs : nullptr,
-                    dev ? nullptr : &status, static_cast<cudaStream_t>(stream), nullptr);
+                    dev ? nullptr : &status, static_cast<cudaStream_t>(stream), nullptr, true);
 }
 
 int ot_assign_solve_stats(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int32_t m,
@@ -658,7 +694,7 @@ int ot_assign_solve_stats(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n,
   int64_t* vs[1] = {v};
   int32_t status = 0;
   int rc = solve_many(ctx, 1, Cs, ld, ns, ms, algo, rs, cost, u ? us : nullptr, v ? vs : nullptr,
-                      &status, static_cast<cudaStream_t>(stream), stats);
+                      &status, static_cast<cudaStream_t>(stream), stats, true);
   if (rc == OT_OK && status != 0) return ctx_fail(ctx, status, "device status error");
   return rc;
 }
@@ -670,7 +706,7 @@ int ot_assign_solve_batched(ot_ctx* ctx, int32_t k, const int32_t* const* C, con
   if (!ctx) return OT_ERR_ARG;
   cudaSetDevice(ctx->device);
   return solve_many(ctx, k, C, ldc, n, m, algo, row_to_col, cost, u, v, status,
-                    static_cast<cudaStream_t>(stream), nullptr);
+                    static_cast<cudaStream_t>(stream), nullptr, false);
 }
 
 int ot_last_call_stats(ot_ctx* ctx, ot_stats* total) {

@@ -21,8 +21,9 @@ constexpr int kNumBuckets = 8;        // bucket b: m <= 32 << b
 constexpr int kMaxGroupCols = 4096;   // widest instance one group engine handles
 constexpr int kForkStreams = 4;
 constexpr int kLargeEngine = -2;  // table entry: use the cluster engine
-// At most this many batched-KM instances wider than kClusterRouteCols in one
-// call go to the cluster engine instead of a group each (API calls only).
+// A batched-KM instance wider than kClusterRouteCols solved on its own
+// (ot_assign_solve / _stats) goes to the cluster engine instead of one group
+// unless the table entry was set explicitly.
 constexpr int kClusterRouteCols = 1024;
 constexpr int kClusterRouteMax = 4;
 int bucket_of(int m);
@@ -52,7 +53,7 @@ struct ServeState;  // ot_serve.cu
 // wave): pinned mirror, device copy, the event that frees the mirror, the
 // per-instance stats block, and cached CUDA graphs keyed by batch layout.
 struct LaunchSlot {
-  DevBuf d_meta, d_stats;
+  DevBuf d_meta, d_stats, d_pack;  // d_pack: 16-bit packed rows of group-engine instances
   PinBuf h_meta;
   cudaEvent_t meta_ev = nullptr;
   bool meta_pending = false;

@@ -162,6 +162,9 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
   const int n = I.n, m = I.m;
   const int32_t* __restrict__ C = I.C;
   const long long ldc = I.ldc;
+  // 16-bit packed rows (row-shifted costs) when the packing pass succeeded
+  const bool pk = I.P != nullptr && *I.pok != 0;
+  const uint16_t* __restrict__ P = I.P;
   int rpar = 0;  // reduction-slot parity
 
   long long dist[K], v[K];
@@ -176,7 +179,10 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
   group_sync<TPI>();
 
   long long init_bytes = 0;
-  if constexpr (ALGO == kAlgoBKM) {
+  if (ALGO == kAlgoBKM && pk) {
+    // B1 on the packed rows: every row minimum is 0 after the shift
+    init_bytes = 4LL * n * m;
+  } else if constexpr (ALGO == kAlgoBKM) {
     // B1: u_i = min_j C[i][j] (v = 0), one warp per row, lanes stride columns.
     constexpr int NW = TPI / 32;
     const int w = t >> 5, l = t & 31;
@@ -234,11 +240,12 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
         const int i = km_row;
         const long long base = level - S.u[i];
         const int32_t* row = C + i * ldc;
+        const uint16_t* prow = P + (long long)i * m;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           const int j = t + k * TPI;
           if (j < m && !((inT >> k) & 1u)) {
-            const long long cand = base + __ldg(row + j) - v[k];
+            const long long cand = base + (pk ? int(__ldg(prow + j)) : __ldg(row + j)) - v[k];
             if (cand < dist[k]) {
               dist[k] = cand;
               pred[k] = i;
@@ -254,11 +261,13 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
 #pragma unroll
           for (int e = 0; e < R; ++e) {
             const int q = q0 + e;
-            const int32_t* row = C + (q < L ? S.list[q] : 0) * ldc;
+            const int ri = q < L ? S.list[q] : 0;
+            const int32_t* row = C + ri * ldc;
+            const uint16_t* prow = P + (long long)ri * m;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
               const int j = t + k * TPI;
-              cc[e][k] = (q < L && j < m && !((inT >> k) & 1u)) ? __ldg(row + j) : 0;
+              cc[e][k] = (q < L && j < m && !((inT >> k) & 1u)) ? (pk ? int(__ldg(prow + j)) : __ldg(row + j)) : 0;
             }
           }
 #pragma unroll
@@ -425,7 +434,10 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
   if (status == kDevOk)
     for (int i = t; i < n; i += TPI) part += __ldg(C + i * ldc + S.r2c[i]);
   const long long cost = group_sum<TPI>(part, S.slots, rpar);
-  for (int i = t; i < n; i += TPI) { I.row_to_col[i] = S.r2c[i]; if (I.u) I.u[i] = S.u[i]; }
+  for (int i = t; i < n; i += TPI) {
+    I.row_to_col[i] = S.r2c[i];
+    if (I.u) I.u[i] = S.u[i] + (pk ? I.roff[i] : 0);
+  }
   if (I.v) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {

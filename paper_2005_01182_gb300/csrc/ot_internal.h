@@ -19,7 +19,20 @@ struct Instance {
   int64_t* cost;        // [1]
   int32_t* status;      // [1]
   int64_t* stats;       // [8], laid out as ot_stats
+  // Optional 16-bit copy of C made by pack_rows: C[i][j] = P[i*m + j] +
+  // roff[i] when *pok != 0 (every row's range fits 16 bits).  The solver then
+  // runs on the row-shifted problem, which has the same assignment and the
+  // same column duals; row duals are shifted back by roff at the end.
+  // (plain struct: every constructor of an Instance sets these, nullptr
+  // when not packed)
+  const uint16_t* P;
+  const int32_t* roff;
+  const int32_t* pok;
 };
+
+// Pack the rows of `num` instances (insts[order[t]], P/roff/pok set) into
+// 16-bit offsets from each row's minimum; one CTA per instance.
+cudaError_t launch_pack(const Instance* insts, const int32_t* order, int num, cudaStream_t stream);
 
 // Shape of a solver group: TPI threads cooperate on one instance, each
 // owning K columns (j = t + k*TPI).  TPI == 32 packs several warps per CTA.

@@ -104,6 +104,9 @@ extern "C" int ot_assign_solve_batched_noalloc(int32_t k, const int32_t* const* 
     I.cost = cost + t;
     I.status = status ? status + t : S->status + t;
     I.stats = nullptr;
+    I.P = nullptr;
+    I.roff = nullptr;
+    I.pok = nullptr;
   }
   // launch order: bucket by bucket, largest instances first
   int off[NB + 1] = {0};

@@ -204,7 +204,7 @@ void ServeState::launch_ready() {
       if (r.algo != algo) continue;
       Layout L(r.n, r.m);
       char* b = arena.base + r.off;
-      Instance I;
+      Instance I = {};
       I.C = reinterpret_cast<const int32_t*>(b + L.c);
       I.ldc = r.m;
       I.n = r.n;

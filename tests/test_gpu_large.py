@@ -96,26 +96,28 @@ def test_single_16384(oracle_mod, ctx):
     assert oracle_mod.check_certificate(C, a2, u2, v2, c2) == 0
 
 
-def test_few_wide_batched_km_take_the_cluster_engine(oracle_mod):
-    """With an untuned table, a call with a handful of batched-KM instances
-    wider than 1024 columns runs them on the cluster engine (and many of
-    them on the group engine); both give certified optima."""
+def test_wide_single_batched_km_takes_the_cluster_engine(oracle_mod):
+    """With an untuned table, a single batched-KM instance wider than 1024
+    columns (ot_assign_solve) runs on the cluster engine, while the batched
+    entry point keeps the group engine; both give certified optima."""
     fresh = ot.Context()
     try:
-        Cs = [W.uniform_costs(n, n + 3, seed=n) for n in (1100, 2047)]
-        dev = [torch.from_numpy(C).cuda() for C in Cs]
-        a = ot.ot_assign_solve_batched(fresh, dev, ot.OT_BKM)
-        torch.cuda.synchronize()
-        for t, C in enumerate(Cs):
-            r, u, v = (x.cpu().numpy() for x in a.outs[t])
-            c = int(a.cost[t])
-            assert oracle_mod.check_certificate(C, r, u, v, c) == 0
+        for n in (1100, 2047):
+            C = W.uniform_costs(n, n + 4, seed=n)
+            a, c, u, v = gpu_solve_on(fresh, C, ot.OT_BKM)
+            assert oracle_mod.check_certificate(C, a, u, v, c) == 0
             assert c == oracle_mod.km(C)[1]
-        many = [W.pixel_sqdist(1030 + 7 * i, seed=i) for i in range(6)]
-        a = ot.ot_assign_solve_batched(fresh, [torch.from_numpy(C).cuda() for C in many], ot.OT_BKM)
+        many = [W.pixel_sqdist(1030 + 7 * i, seed=i) for i in range(3)]
+        b = ot.ot_assign_solve_batched(fresh, [torch.from_numpy(C).cuda() for C in many], ot.OT_BKM)
         torch.cuda.synchronize()
         for t, C in enumerate(many):
-            r, u, v = (x.cpu().numpy() for x in a.outs[t])
-            assert oracle_mod.check_certificate(C, r, u, v, int(a.cost[t])) == 0
+            r, u, v = (x.cpu().numpy() for x in b.outs[t])
+            assert oracle_mod.check_certificate(C, r, u, v, int(b.cost[t])) == 0
     finally:
         fresh.close()
+
+
+def gpu_solve_on(c, C, algo):
+    r, cost, u, v = ot.ot_assign_solve(c, torch.from_numpy(np.ascontiguousarray(C)).cuda(), algo)
+    torch.cuda.synchronize()
+    return r.cpu().numpy(), int(cost.item()), u.cpu().numpy(), v.cpu().numpy()
