@@ -200,13 +200,27 @@ def measure_single_16384(ctx, stream, ot, torch):
             best = (t, st, int(c.item()))
     t, st, cost = best
     alg = st["cost_bytes"] + st["init_bytes"]
+    # the paper's approximate variant: one scaling factor s (s = 16 keeps the
+    # a-priori bound n*(s-1) within 10 % of the optimum here)
+    scaled = {}
+    for sc in (16, 64):
+        ot.ot_assign_solve_scaled(ctx, Cd, sc, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r2, c2, bnd = ot.ot_assign_solve_scaled(ctx, Cd, sc, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        scaled[str(sc)] = {"s_per_solve": e0.elapsed_time(e1) / 1000.0, "cost": int(c2.item()),
+                           "ratio_to_opt": int(c2.item()) / cost, "bound": bnd, "bound_ratio": 1 + bnd / cost}
     del Cd
     torch.cuda.empty_cache()
     return {"algo": "batched KM", "s_per_solve": t, "solves_per_s": 1.0 / t, "cost": cost,
             "algorithmic_bytes": alg, "achieved_gbs": alg / t / 1e9,
             "hbm_frac": alg / t / 1e9 / peak, "peak_gbs": peak, "peak_kind": kind,
             "hbm_frac_vs_8tbs": alg / t / 1e9 / 8000.0,
-            "steps": st["steps"], "phases": st["phases"], "rows_scanned": st["rows_scanned"]}
+            "steps": st["steps"], "phases": st["phases"], "rows_scanned": st["rows_scanned"],
+            "scaled_batched_km": scaled}
 
 
 def measure_served(ctx_unused, stream, ot, torch, dev, args):
@@ -308,8 +322,9 @@ def main():
     ap.add_argument("--skip-extras", action="store_true")
     ap.add_argument("--served-requests", type=int, default=1500)
     ap.add_argument("--profile-once", default=None, choices=["batch", "n16384", "n8192"],
-                    help="untimed single run for an ncu capture: 'batch' = 3 batched KM calls on the "
-                         "4096-instance batch; 'n16384' / 'n8192' = one batched-KM solve on a grid instance")
+                    help="untimed single run for an ncu capture: 'batch' = autotune, then 3 batched "
+                         "OT_AUTO calls on the 4096-instance batch inside an NVTX range 'timed'; "
+                         "'n16384' / 'n8192' = one batched-KM solve on a grid instance")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -347,10 +362,17 @@ def main():
     Cs = batch_for_rank(rank, args.k)
     dC = [torch.from_numpy(C).to(dev) for C in Cs]
     if args.profile_once:
+        # the timed configuration: tuned table, OT_AUTO; the three calls sit
+        # in an NVTX range "timed" for ncu --nvtx-include
+        ot.ot_autotune(ctx, dC, ot.OT_AUTO, repeats=1)
         a = ot.BatchArgs(dC)
-        for _ in range(3):
-            ot.ot_assign_solve_batched(ctx, a, ot.OT_KM, stream)
+        ot.ot_assign_solve_batched(ctx, a, ot.OT_AUTO, stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
+        for _ in range(3):
+            ot.ot_assign_solve_batched(ctx, a, ot.OT_AUTO, stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         assert (a.status.cpu().numpy() == 0).all()
         ctx.close()
         return

@@ -106,6 +106,19 @@ int ot_assign_solve_stats(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n,
                           int32_t m, int32_t algo, int32_t* row_to_col, int64_t* cost,
                           int64_t* u, int64_t* v, ot_stats* stats, void* stream);
 
+/* Batched KM with a single scaling factor s >= 1, the paper's approximate
+ * variant (Sec. 2.3 "Batched KM": costs rounded to small integers by one
+ * factor; Table 4 runs it as a 1.1-approximation).  The assignment problem
+ * is solved exactly on the scaled costs floor(C[i][j] / s) and the result's
+ * cost under the original C is returned in *cost.  Writing
+ * c = s*floor(c/s) + r with 0 <= r <= s-1 gives
+ * OPT <= *cost <= OPT + n*(s-1); *bound (may be NULL) receives n*(s-1).
+ * s = 1 is the exact solver.  Synchronous.  C, row_to_col, cost and bound
+ * may be host or device pointers. */
+int ot_assign_solve_scaled(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int32_t m,
+                           int32_t scale, int32_t* row_to_col, int64_t* cost, int64_t* bound,
+                           void* stream);
+
 /* Synchronise the context's stream and return the counters of the most
  * recent ot_assign_solve / ot_assign_solve_batched call on device pointers,
  * summed over its instances; reserved[0] receives the number of kernel

@@ -653,6 +653,7 @@ void ot_ctx_destroy(ot_ctx* ctx) {
   ctx->d_io.release();
   ctx->d_scratch.release();
   ctx->d_large.release();
+  ctx->d_scaled.release();
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }

@@ -74,7 +74,8 @@ struct ot_ctx {
   std::mutex api_mu;
 
   LaunchSlot api;
-  DevBuf d_status, d_io, d_scratch, d_large;
+  DevBuf d_status, d_io, d_scratch, d_large, d_scaled;
+  std::mutex scaled_mu;
 
   int table[2][ot::kNumBuckets];
   bool tuned[2][ot::kNumBuckets] = {};  // entry set by ot_tune_set / ot_autotune / tune file

@@ -95,6 +95,7 @@ def load(path: str | None = None):
         "ot_assign_solve_batched_noalloc": (ctypes.c_int, [i32, pp, ctypes.POINTER(i64),
                                                            ctypes.POINTER(i32), ctypes.POINTER(i32), i32,
                                                            pp, vp, pp, pp, vp, vp]),
+        "ot_assign_solve_scaled": (ctypes.c_int, [vp, vp, i64, i32, i32, i32, vp, vp, vp, vp]),
         "ot_version": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -243,6 +244,19 @@ def ot_assign_solve_batched(ctx: Context, Cs_or_args, algo: int = OT_KM, stream=
                                          _ptr(a.status), _stream_handle(stream))
     ctx._raise(rc, "ot_assign_solve_batched")
     return a
+
+
+def ot_assign_solve_scaled(ctx: Context, C: torch.Tensor, scale: int, stream=None):
+    """Batched KM on floor(C / scale): returns (row_to_col, cost under C,
+    a-priori bound n*(scale-1) on cost - OPT)."""
+    n, m, ldc = _check_cost(C)
+    r = torch.empty(n, dtype=torch.int32, device=C.device)
+    c = torch.empty(1, dtype=torch.int64, device=C.device)
+    b = torch.empty(1, dtype=torch.int64)
+    rc = ctx.lib.ot_assign_solve_scaled(ctx.h, _ptr(C), ldc, n, m, scale, _ptr(r), _ptr(c), _ptr(b),
+                                        _stream_handle(stream))
+    ctx._raise(rc, "ot_assign_solve_scaled")
+    return r, c, int(b.item())
 
 
 def ot_last_call_stats(ctx: Context) -> dict:

@@ -256,3 +256,23 @@ def test_pins_catch_planted_mistakes(oracle_mod, idx):
 
 if __name__ == "__main__" and len(sys.argv) == 5 and sys.argv[1] == "--mutant-check":
     _mutant_check(sys.argv[2], sys.argv[3], int(sys.argv[4]))
+
+
+def test_single_scaling_factor_bound(oracle_mod):
+    """The paper's approximate batched KM solves floor(C/s) exactly; with
+    c = s*floor(c/s) + r, 0 <= r <= s-1, the assignment it returns costs at
+    most OPT + n*(s-1) under C.  Checked against brute force."""
+    r = np.random.default_rng(21)
+    for trial in range(300):
+        n = int(r.integers(1, 7))
+        m = n + int(r.integers(0, 2))
+        C = r.integers(-500, 5000, size=(n, m)).astype(np.int32)
+        _, opt = oracle_mod.brute_force(C)
+        for s in (1, 2, 7, 100, 4096):
+            Cs = np.floor_divide(C, s).astype(np.int32)
+            a, cs, u, v = oracle_mod.bkm(Cs)
+            true = int(C[np.arange(n), a].astype(np.int64).sum())
+            assert cs == oracle_mod.brute_force(Cs)[1]
+            assert opt <= true <= opt + n * (s - 1)
+            if s == 1:
+                assert true == opt
