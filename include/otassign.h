@@ -119,6 +119,20 @@ int ot_assign_solve_scaled(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n
                            int32_t scale, int32_t* row_to_col, int64_t* cost, int64_t* bound,
                            void* stream);
 
+/* Optimal transport with integer supplies and demands (Sec. 1, Eq. 1:
+ * min <C, X> subject to X 1 = r, X^T 1 = c with nonnegative integer r, c),
+ * solved exactly by vertex replication: row i is copied supply[i] times and
+ * column j demand[j] times, the R x M assignment problem (R = sum(supply) <=
+ * M = sum(demand)) is solved with `algo`, and flow[i*m + j] counts the
+ * matched copies of (i, j).  With equal totals this is Eq. 1; with
+ * R < M every column receives at most demand[j].  *cost = <C, X>.  Only
+ * small totals are practical: OT_ERR_UNSUPPORTED if M > 65536 or
+ * R*M > 2^30.  supply and demand are host arrays; C, flow (n*m int32) and
+ * cost may be host or device pointers.  Synchronous. */
+int ot_transport_solve(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int32_t m,
+                       const int32_t* supply, const int32_t* demand, int32_t algo, int64_t* cost,
+                       int32_t* flow, void* stream);
+
 /* Synchronise the context's stream and return the counters of the most
  * recent ot_assign_solve / ot_assign_solve_batched call on device pointers,
  * summed over its instances; reserved[0] receives the number of kernel

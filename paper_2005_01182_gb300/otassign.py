@@ -96,6 +96,7 @@ def load(path: str | None = None):
                                                            ctypes.POINTER(i32), ctypes.POINTER(i32), i32,
                                                            pp, vp, pp, pp, vp, vp]),
         "ot_assign_solve_scaled": (ctypes.c_int, [vp, vp, i64, i32, i32, i32, vp, vp, vp, vp]),
+        "ot_transport_solve": (ctypes.c_int, [vp, vp, i64, i32, i32, vp, vp, i32, vp, vp, vp]),
         "ot_version": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -257,6 +258,22 @@ def ot_assign_solve_scaled(ctx: Context, C: torch.Tensor, scale: int, stream=Non
                                         _stream_handle(stream))
     ctx._raise(rc, "ot_assign_solve_scaled")
     return r, c, int(b.item())
+
+
+def ot_transport_solve(ctx: Context, C: torch.Tensor, supply, demand, algo: int = OT_AUTO, stream=None):
+    """Integer-supply transport by vertex replication: returns (flow n x m
+    int32 on C's device, cost)."""
+    import numpy as np
+    n, m, ldc = _check_cost(C)
+    sp = np.ascontiguousarray(supply, dtype=np.int32)
+    dm = np.ascontiguousarray(demand, dtype=np.int32)
+    flow = torch.empty((n, m), dtype=torch.int32, device=C.device)
+    c = torch.empty(1, dtype=torch.int64)
+    rc = ctx.lib.ot_transport_solve(ctx.h, _ptr(C), ldc, n, m, ctypes.c_void_p(sp.ctypes.data),
+                                    ctypes.c_void_p(dm.ctypes.data), algo, _ptr(c), _ptr(flow),
+                                    _stream_handle(stream))
+    ctx._raise(rc, "ot_transport_solve")
+    return flow, int(c.item())
 
 
 def ot_last_call_stats(ctx: Context) -> dict:

@@ -1,0 +1,62 @@
+"""GPU integer-supply transport (vertex replication) against an LP optimum."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2005_01182_gb300 import otassign as ot
+from paper_2005_01182_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _lp(C, r, c):
+    from scipy.optimize import linprog
+    n, m = C.shape
+    A_eq = np.zeros((n, n * m))
+    for i in range(n):
+        A_eq[i, i * m:(i + 1) * m] = 1
+    A_ub = np.zeros((m, n * m))
+    for j in range(m):
+        A_ub[j, j::m] = 1
+    res = linprog(C.astype(np.float64).ravel(), A_ub=A_ub, b_ub=c, A_eq=A_eq, b_eq=r, bounds=(0, None),
+                  method="highs")
+    return int(round(res.fun))
+
+
+@pytest.mark.parametrize("algo", [ot.OT_KM, ot.OT_BKM, ot.OT_AUTO])
+def test_transport_matches_lp(ctx, algo):
+    rng = np.random.default_rng(7 + algo)
+    for trial in range(12):
+        n, m = int(rng.integers(1, 15)), int(rng.integers(1, 15))
+        r = rng.integers(0, 12, n)
+        c = rng.integers(0, 14, m)
+        if r.sum() > c.sum():
+            c[-1] += r.sum() - c.sum()
+        C = rng.integers(0, 500, size=(n, m)).astype(np.int32)
+        for dev in (True, False):
+            Ct = torch.from_numpy(C).cuda() if dev else torch.from_numpy(C)
+            flow, cost = ot.ot_transport_solve(ctx, Ct, r, c, algo)
+            X = flow.cpu().numpy().astype(np.int64)
+            assert (X >= 0).all()
+            np.testing.assert_array_equal(X.sum(1), r)
+            assert (X.sum(0) <= c).all()
+            assert int((X * C).sum()) == cost
+            assert cost == _lp(C, r, c)
+
+
+def test_transport_mnist_like(ctx):
+    """Two 'images': pixel positions on a 28 x 28 grid with small integer
+    intensities as supplies/demands, squared-distance costs."""
+    rng = np.random.default_rng(3)
+    pa = rng.choice(784, 40, replace=False)
+    pb = rng.choice(784, 45, replace=False)
+    r = rng.integers(1, 8, 40)
+    c = rng.integers(1, 8, 45)
+    c[0] += max(0, r.sum() - c.sum())
+    a = np.stack([pa // 28, pa % 28], 1)
+    b = np.stack([pb // 28, pb % 28], 1)
+    C = ((a[:, None, :] - b[None, :, :]) ** 2).sum(-1).astype(np.int32)
+    flow, cost = ot.ot_transport_solve(ctx, torch.from_numpy(C).cuda(), r, c)
+    X = flow.cpu().numpy()
+    np.testing.assert_array_equal(X.sum(1), r)
+    assert cost == _lp(C, r, c)

@@ -276,3 +276,40 @@ def test_single_scaling_factor_bound(oracle_mod):
             assert opt <= true <= opt + n * (s - 1)
             if s == 1:
                 assert true == opt
+
+
+def _transport_lp(C, r, c):
+    """Optimal value of min <C, X>, X 1 = r, X^T 1 <= c, X >= 0 (scipy LP;
+    integral at the optimum for integer r, c)."""
+    from scipy.optimize import linprog
+    n, m = C.shape
+    A_eq = np.zeros((n, n * m))
+    for i in range(n):
+        A_eq[i, i * m:(i + 1) * m] = 1
+    A_ub = np.zeros((m, n * m))
+    for j in range(m):
+        A_ub[j, j::m] = 1
+    res = linprog(C.astype(np.float64).ravel(), A_ub=A_ub, b_ub=c, A_eq=A_eq, b_eq=r, bounds=(0, None),
+                  method="highs")
+    assert res.status == 0
+    return int(round(res.fun))
+
+
+def test_transport_by_replication(oracle_mod):
+    """Vertex replication turns integer-supply transport (Eq. 1) into an
+    assignment problem with the same optimum (checked against an LP)."""
+    rng = np.random.default_rng(31)
+    for trial in range(40):
+        n, m = int(rng.integers(1, 6)), int(rng.integers(1, 7))
+        r = rng.integers(0, 5, n)
+        c = rng.integers(0, 6, m)
+        if r.sum() > c.sum():
+            c[0] += r.sum() - c.sum()
+        C = rng.integers(-20, 100, size=(n, m)).astype(np.int32)
+        rows = np.repeat(np.arange(n), r)
+        cols = np.repeat(np.arange(m), c)
+        if len(rows) == 0:
+            continue
+        rep = C[np.ix_(rows, cols)]
+        cost = oracle_mod.km(rep)[1]
+        assert cost == _transport_lp(C, r, c)
