@@ -453,7 +453,9 @@ def main():
     line = None
     if rank == 0:
         peak, peak_kind = _peaks()
-        alg_bytes = st["cost_bytes"] + st["init_bytes"]
+        # algorithmic bytes: cost elements the scans must read (2 bytes each
+        # for rows packed to 16 bits) plus the batched-KM row reduction
+        alg_bytes = (st.get("read_bytes") or st["cost_bytes"]) + st["init_bytes"]
         kern_ms = float(np.mean(step_ms))
         achieved = alg_bytes / (kern_ms / 1000.0) / 1e9
         line = {

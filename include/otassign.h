@@ -76,7 +76,9 @@ typedef struct ot_stats {
   int64_t phases;         /* KM: rows rooted; BKM: dual-adjust/augment phases */
   int64_t augmentations;  /* augmenting paths applied */
   int64_t init_bytes;     /* BKM row-reduction pass bytes (4*n*m), else 0 */
-  int64_t reserved[2];
+  int64_t reserved[2];    /* [1]: bytes of cost elements actually loaded by the
+                             scans (2 per element when rows were packed to
+                             16 bits, else equal to cost_bytes) */
 } ot_stats;
 
 typedef struct ot_config {

@@ -731,6 +731,7 @@ int ot_last_call_stats(ot_ctx* ctx, ot_stats* total) {
       total->phases += h[t * 8 + 3];
       total->augmentations += h[t * 8 + 4];
       total->init_bytes += h[t * 8 + 5];
+      total->reserved[1] += h[t * 8 + 7];
     }
   }
   total->reserved[0] = ctx->api.last_launches;

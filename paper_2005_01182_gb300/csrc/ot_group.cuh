@@ -201,6 +201,7 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
   group_sync<TPI>();
 
   long long steps = 0, rows = 0, bytes = 0, phases = 0, augs = 0;
+  long long read_bytes = 0;  // bytes of cost elements actually loaded (2 when packed)
   int status = kDevOk;
   int matched = 0;
   int p = 0;  // list-counter parity (batched KM)
@@ -290,6 +291,7 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
       ++steps;
       rows += L;
       bytes += 4LL * L * (m - tcount);
+      read_bytes += (pk ? 2LL : 4LL) * L * (m - tcount);
 
       // A2 / B4: minimum distance outside T, lowest column on ties
       Best b{kInf, INT_MAX};
@@ -454,6 +456,8 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
       I.stats[3] = phases;
       I.stats[4] = augs;
       I.stats[5] = init_bytes;
+      I.stats[6] = 0;
+      I.stats[7] = read_bytes;
     }
   }
   // results before the status word, at system scope: a host thread that

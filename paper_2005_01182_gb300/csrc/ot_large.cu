@@ -970,8 +970,11 @@ __global__ void large_final(LargeWs w, Instance I) {
   if ((threadIdx.x & 31) == 0 && part) atomicAdd(reinterpret_cast<unsigned long long*>(I.cost), (unsigned long long)part);
   if (tid == 0) {
     if (I.status) *I.status = ok ? 0 : (w.ctl->status ? w.ctl->status : kDevStepLimit);
-    if (I.stats)
+    if (I.stats) {
       for (int q = 0; q < 6; ++q) I.stats[q] = (long long)w.ctl->stats[q];
+      I.stats[6] = 0;
+      I.stats[7] = (long long)w.ctl->stats[2];  // 4-byte elements: read bytes = cost bytes
+    }
   }
 }
 

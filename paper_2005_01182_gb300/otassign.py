@@ -203,6 +203,7 @@ def ot_assign_solve_stats(ctx: Context, C: torch.Tensor, algo: int = OT_KM, stre
                                        _ptr(v), ctypes.byref(st), _stream_handle(stream))
     ctx._raise(rc, "ot_assign_solve_stats")
     stats = {f: getattr(st, f) for f, _ in ot_stats._fields_ if f != "reserved"}
+    stats["read_bytes"] = st.reserved[1]
     return r, c, u, v, stats
 
 
@@ -283,6 +284,7 @@ def ot_last_call_stats(ctx: Context) -> dict:
     ctx._raise(ctx.lib.ot_last_call_stats(ctx.h, ctypes.byref(st)), "ot_last_call_stats")
     d = {f: getattr(st, f) for f, _ in ot_stats._fields_ if f != "reserved"}
     d["launches"] = st.reserved[0]
+    d["read_bytes"] = st.reserved[1]
     return d
 
 
