@@ -33,8 +33,12 @@
  * the library asks the CUDA runtime which one it is.  Host inputs are copied
  * to device staging owned by the context and host outputs are written back
  * before the call returns.  With device pointers the call is asynchronous on
- * `stream` (a cudaStream_t; NULL means the context's own stream) unless
- * stated otherwise; the caller keeps ownership of all buffers and the
+ * `stream` (a cudaStream_t) unless stated otherwise.  NULL (like the legacy
+ * and per-thread default-stream handles) means the caller's default stream:
+ * the library then works on a stream of its own that is ordered after the
+ * work already queued on the default stream and before the work queued
+ * there after the call.  Consecutive calls on one context are ordered among
+ * themselves whatever streams they name.  The caller keeps ownership of all buffers and the
  * library keeps no caller pointer after the call returns.  The cost matrix is
  * row-major int32 with leading dimension ldc (elements, ldc >= m).
  *

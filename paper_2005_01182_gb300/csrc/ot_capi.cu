@@ -265,22 +265,16 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
   const size_t work_bytes = al256(sizeof(int) * (nb + 1));
   const size_t total = desc_bytes + order_bytes + work_bytes;
 
-  // the pinned mirror may still feed the previous call's copy
-  if (slot.meta_pending) {
-    cudaEventSynchronize(slot.meta_ev);
-    slot.meta_pending = false;
-  }
-  if (int rc = slot.h_meta.reserve(total); rc) return ctx_fail(ctx, rc, "pinned alloc");
   const int gen = slot.d_meta.generation;
   if (int rc = slot.d_meta.reserve(total); rc) return ctx_fail(ctx, rc, "meta alloc");
   if (slot.d_meta.generation != gen) slot.clear_graphs();
 
-  char* h = static_cast<char*>(slot.h_meta.ptr);
-  char* d = static_cast<char*>(slot.d_meta.ptr);
-  std::memcpy(h, insts.data(), sizeof(Instance) * k);
-  int32_t* horder = reinterpret_cast<int32_t*>(h + desc_bytes);
-  int* hwork = reinterpret_cast<int*>(h + desc_bytes + order_bytes);
-  std::memset(hwork, 0, work_bytes);
+  // descriptors and launch order, built on the host and uploaded only when
+  // they differ from what the device already holds
+  std::vector<char>& pend = slot.pending;
+  pend.assign(desc_bytes + order_bytes, 0);
+  std::memcpy(pend.data(), insts.data(), sizeof(Instance) * k);
+  int32_t* horder = reinterpret_cast<int32_t*>(pend.data() + desc_bytes);
   std::string key = std::to_string(algo) + "|" + std::to_string(k);
   std::vector<int> offs;
   int off = 0;
@@ -293,12 +287,33 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
   }
   key += "|" + std::to_string(reinterpret_cast<uintptr_t>(stream)) + (any_pack ? "|p" : "");
 
+  char* d = static_cast<char*>(slot.d_meta.ptr);
   const Instance* dinst = reinterpret_cast<const Instance*>(d);
   const int32_t* dorder = reinterpret_cast<const int32_t*>(d + desc_bytes);
   int* dwork = reinterpret_cast<int*>(d + desc_bytes + order_bytes);
 
+  // the slot's buffers (descriptors, work counters, packed rows, stats) are
+  // reused: this launch starts after the previous one, on whatever stream
+  if (slot.meta_pending) {
+    if (cudaError_t e = cudaStreamWaitEvent(stream, slot.meta_ev, 0); e != cudaSuccess)
+      return ctx_cuda(ctx, e, "order after previous launch");
+  }
+  if (!(slot.meta_valid && pend == slot.last_meta)) {
+    // the pinned mirror may still feed the previous upload
+    if (slot.meta_pending) cudaEventSynchronize(slot.meta_ev);
+    if (int rc = slot.h_meta.reserve(pend.size()); rc) return ctx_fail(ctx, rc, "pinned alloc");
+    std::memcpy(slot.h_meta.ptr, pend.data(), pend.size());
+    if (cudaError_t e = cudaMemcpyAsync(d, slot.h_meta.ptr, pend.size(), cudaMemcpyHostToDevice, stream);
+        e != cudaSuccess) {
+      slot.meta_valid = false;
+      return ctx_cuda(ctx, e, "descriptor upload");
+    }
+    slot.last_meta.swap(pend);
+    slot.meta_valid = true;
+  }
+
   auto enqueue = [&](cudaStream_t s) -> cudaError_t {
-    cudaError_t e = cudaMemcpyAsync(d, h, total, cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaMemsetAsync(dwork, 0, work_bytes, s);
     if (e != cudaSuccess) return e;
     if (any_pack && (e = launch_pack(dinst, nullptr, k, s)) != cudaSuccess) return e;
     if (nb == 1 || !fork) {
@@ -355,11 +370,10 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
   } else {
     e = enqueue(stream);
   }
+  // marks the end of this launch and of the descriptor upload
+  cudaEventRecord(slot.meta_ev, stream);
+  slot.meta_pending = true;
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "batch launch");
-  if (nb > 0) {
-    cudaEventRecord(slot.meta_ev, stream);
-    slot.meta_pending = true;
-  }
   slot.last_launches = nb;
   return OT_OK;
 }
@@ -384,8 +398,6 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
   if (k < 0) return ctx_fail(ctx, OT_ERR_ARG, "k < 0");
   if (k == 0) return OT_OK;
   if (!C || !ldc || !n || !m || !r2c || !cost) return ctx_fail(ctx, OT_ERR_ARG, "null array");
-  if (!stream) stream = ctx->stream;
-
   // all element pointers must live on one side
   int first = -1;
   for (int t = 0; t < k; ++t)
@@ -402,6 +414,8 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
 
   std::vector<Instance> insts(k);
   std::lock_guard<std::mutex> lock(ctx->api_mu);
+  StreamScope scope(stream, ctx->stream, ctx->join_in_ev, ctx->join_out_ev);
+  stream = scope.work;
   cudaError_t e;
   if (dev) {
     // device pointers: cost/status arrays are device arrays of length k
@@ -585,6 +599,26 @@ int LaunchSlot::init() {
 void LaunchSlot::clear_graphs() {
   for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
   graphs.clear();
+  meta_valid = false;
+}
+
+static bool is_default_stream(cudaStream_t s) {
+  return s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread;
+}
+
+StreamScope::StreamScope(cudaStream_t given, cudaStream_t own, cudaEvent_t in_ev, cudaEvent_t out)
+    : user(given), work(given) {
+  if (!is_default_stream(given)) return;
+  work = own;
+  out_ev = out;
+  cudaEventRecord(in_ev, given ? given : cudaStreamLegacy);
+  cudaStreamWaitEvent(own, in_ev, 0);
+}
+
+StreamScope::~StreamScope() {
+  if (!out_ev) return;
+  cudaEventRecord(out_ev, work);
+  cudaStreamWaitEvent(user ? user : cudaStreamLegacy, out_ev, 0);
 }
 
 void LaunchSlot::release() {
@@ -624,6 +658,8 @@ int ot_ctx_create(ot_ctx** out, const ot_config* cfg) {
     cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming);
   }
   cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+  for (cudaEvent_t* ev : {&ctx->join_in_ev, &ctx->join_out_ev, &ctx->sjoin_in_ev, &ctx->sjoin_out_ev})
+    if (cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess) { ot_ctx_destroy(ctx); return OT_ERR_CUDA; }
   if (ctx->api.init() != OT_OK) { ot_ctx_destroy(ctx); return OT_ERR_CUDA; }
   ctx->api.use_graphs = true;
   default_table(ctx->table);
@@ -649,6 +685,8 @@ void ot_ctx_destroy(ot_ctx* ctx) {
     if (ctx->join_ev[i]) cudaEventDestroy(ctx->join_ev[i]);
   }
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  for (cudaEvent_t ev : {ctx->join_in_ev, ctx->join_out_ev, ctx->sjoin_in_ev, ctx->sjoin_out_ev})
+    if (ev) cudaEventDestroy(ev);
   ctx->d_status.release();
   ctx->d_io.release();
   ctx->d_scratch.release();
@@ -782,6 +820,8 @@ int ot_autotune(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* 
   cudaSetDevice(ctx->device);
   repeats = std::max(1, repeats);
   std::lock_guard<std::mutex> lock(ctx->api_mu);
+  // the instances may still be in flight on any of the caller's streams
+  if (cudaError_t e = cudaDeviceSynchronize(); e != cudaSuccess) return ctx_cuda(ctx, e, "autotune sync");
   // scratch outputs for every instance
   size_t total = al256(sizeof(int64_t) * k) + al256(sizeof(int32_t) * k);
   std::vector<size_t> off(k);

@@ -50,13 +50,18 @@ struct PinBuf {
 struct ServeState;  // ot_serve.cu
 
 // Descriptor upload buffers of one launcher (the API path, or one serving
-// wave): pinned mirror, device copy, the event that frees the mirror, the
-// per-instance stats block, and cached CUDA graphs keyed by batch layout.
+// wave): pinned mirror, device copy, the event that marks the end of the
+// slot's latest launch, the per-instance stats block, and cached CUDA graphs
+// keyed by batch layout.  The descriptors are uploaded only when they differ
+// from the ones already on the device (last_meta), so that a caller who
+// re-issues the same batch never waits on the host for the previous launch.
 struct LaunchSlot {
   DevBuf d_meta, d_stats, d_pack;  // d_pack: 16-bit packed rows of group-engine instances
   PinBuf h_meta;
   cudaEvent_t meta_ev = nullptr;
   bool meta_pending = false;
+  std::vector<char> last_meta, pending;  // descriptor bytes on the device / being built
+  bool meta_valid = false;               // last_meta matches d_meta
   bool use_graphs = false;
   std::map<std::string, cudaGraphExec_t> graphs;
   int last_launches = 0;
@@ -70,6 +75,10 @@ struct ot_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t bstreams[ot::kForkStreams] = {};
   cudaEvent_t fork_ev = nullptr, join_ev[ot::kForkStreams] = {};
+  // ordering with the caller's default stream (StreamScope): one pair for
+  // the calls serialised by api_mu, one for those serialised by scaled_mu
+  cudaEvent_t join_in_ev = nullptr, join_out_ev = nullptr;
+  cudaEvent_t sjoin_in_ev = nullptr, sjoin_out_ev = nullptr;
   std::string err;
   std::mutex api_mu;
 
@@ -86,6 +95,22 @@ struct ot_ctx {
   std::vector<int> last_skip;   // which of them were not launched
 
   ServeState* serve = nullptr;
+};
+
+// The stream an API call works on.  A NULL handle (or the legacy or
+// per-thread default-stream handle) names the caller's default stream, on
+// which graphs cannot be captured: the call then works on the context's own
+// stream, which first waits for the work already queued on the default
+// stream; on leaving the scope the default stream waits for the call's work.
+// The events belong to the lock domain the caller holds.
+struct StreamScope {
+  cudaStream_t user = nullptr;  // as given
+  cudaStream_t work = nullptr;  // where the call enqueues
+  cudaEvent_t out_ev = nullptr;
+  StreamScope(cudaStream_t given, cudaStream_t own, cudaEvent_t in_ev, cudaEvent_t out);
+  ~StreamScope();
+  StreamScope(const StreamScope&) = delete;
+  StreamScope& operator=(const StreamScope&) = delete;
 };
 
 int ctx_fail(ot_ctx* ctx, int code, const std::string& msg);

@@ -45,7 +45,9 @@ extern "C" int ot_assign_solve_scaled(ot_ctx* ctx, const int32_t* C, int64_t ldc
   if (scale < 1 || n < 0 || m < n || (n > 0 && (!C || ldc < m || !row_to_col)) || !cost)
     return ctx_fail(ctx, OT_ERR_ARG, "bad arguments");
   cudaSetDevice(ctx->device);
-  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+  std::lock_guard<std::mutex> lock(ctx->scaled_mu);
+  StreamScope scope(static_cast<cudaStream_t>(stream), ctx->stream, ctx->sjoin_in_ev, ctx->sjoin_out_ev);
+  cudaStream_t s = scope.work;
   const bool dev = n > 0 ? ptr_on_device(C) : ptr_on_device(cost);
   if (bound) {
     const int64_t b = int64_t(n) * (scale - 1);
@@ -65,7 +67,6 @@ extern "C" int ot_assign_solve_scaled(ot_ctx* ctx, const int32_t* C, int64_t ldc
   const size_t o_v = o_u + ((8 * size_t(n) + 255) & ~size_t(255));
   const size_t o_cost = o_v + ((8 * size_t(m) + 255) & ~size_t(255));
   const size_t total = o_cost + 256;
-  std::lock_guard<std::mutex> lock(ctx->scaled_mu);
   if (int rc = ctx->d_scaled.reserve(total); rc) return ctx_fail(ctx, rc, "scaled workspace");
   char* B = static_cast<char*>(ctx->d_scaled.ptr);
   const int32_t* Cd = C;

@@ -49,7 +49,9 @@ extern "C" int ot_transport_solve(ot_ctx* ctx, const int32_t* C, int64_t ldc, in
   if (M > 65536 || R * M > (1LL << 30))
     return ctx_fail(ctx, OT_ERR_UNSUPPORTED, "replicated problem too large");
   cudaSetDevice(ctx->device);
-  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+  std::lock_guard<std::mutex> lock(ctx->scaled_mu);
+  StreamScope scope(static_cast<cudaStream_t>(stream), ctx->stream, ctx->sjoin_in_ev, ctx->sjoin_out_ev);
+  cudaStream_t s = scope.work;
   const bool dev = n > 0 ? ptr_on_device(C) : false;
   const bool dflow = n > 0 && ptr_on_device(flow);
   if (R == 0) {
@@ -78,7 +80,6 @@ extern "C" int ot_transport_solve(ot_ctx* ctx, const int32_t* C, int64_t ldc, in
   const size_t o_v = off; off += al(8 * size_t(M));
   const size_t o_flow = off; off += al(4 * size_t(n) * m);
   const size_t o_cost = off; off += 256;
-  std::lock_guard<std::mutex> lock(ctx->scaled_mu);
   if (int rc = ctx->d_scaled.reserve(off); rc) return ctx_fail(ctx, rc, "transport workspace");
   char* B = static_cast<char*>(ctx->d_scaled.ptr);
   const int32_t* Cd = C;

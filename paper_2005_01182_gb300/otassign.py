@@ -112,8 +112,12 @@ def _ptr(t):
 
 
 def _stream_handle(stream) -> ctypes.c_void_p | None:
+    """The stream a call is issued on: the given one, else torch's current
+    stream (handle 0, the default stream, is ordered by the library)."""
     if stream is None:
-        return None
+        if not torch.cuda.is_available():
+            return None
+        stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
