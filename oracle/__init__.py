@@ -15,6 +15,10 @@ What each function follows in the paper:
   * ``bkm``          -- batched KM, exact mode (Sec. 2.3 "Batched KM").
   * ``check_certificate`` -- LP duality for Eq. 1 (weak duality makes a
     feasible dual with equal objective a proof of optimality).
+  * ``auction``      -- the auction algorithm with epsilon-scaling in
+    parallel (Jacobi) rounds (Sec. 2.3.3 "The auction algorithm", Sec. 4.1
+    "Auction"), exact for integer costs by scaling them by N + 1 and
+    finishing at epsilon = 1.
 
 Parity is pinned for every function (brute force over permutations, closed
 forms, scipy's ``linear_sum_assignment``, the certificate); see
@@ -71,6 +75,8 @@ def _load():
             f.argtypes = [i32p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, i32p, i64p, i64p, i64p]
         lib.oracle_brute_force.restype = ctypes.c_int64
         lib.oracle_brute_force.argtypes = [i32p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, i32p]
+        lib.oracle_auction.restype = ctypes.c_int64
+        lib.oracle_auction.argtypes = [i32p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, i32p, i64p, i64p]
         lib.oracle_check_certificate.restype = ctypes.c_int
         lib.oracle_check_certificate.argtypes = [i32p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                                  i32p, i64p, i64p, ctypes.c_int64]
@@ -126,6 +132,25 @@ def bkm(C, stats: bool = False):
     if stats:
         return out + ({"rounds": int(st[0]), "phases": int(st[1]), "augmentations": int(st[2]),
                        "bytes": int(st[3])},)
+    return out
+
+
+def auction(C, stats: bool = False):
+    """Exact auction with epsilon-scaling.  Returns (row_to_col int32[n],
+    cost, prices int64[m] in scaled units) and, with ``stats``, {stages,
+    rounds, bids, real_bids}."""
+    C, n, m = _as_cost(C)
+    a = np.empty(n, np.int32)
+    p = np.zeros(m, np.int64)
+    st = np.zeros(4, np.int64)
+    cost = _load().oracle_auction(_p(C, ctypes.c_int32), m, n, m, _p(a, ctypes.c_int32),
+                                  _p(p, ctypes.c_int64), _p(st, ctypes.c_int64))
+    if cost == np.iinfo(np.int64).min:
+        raise ValueError("oracle_auction failed (allocation or scaled range above 2^50)")
+    out = (a, int(cost), p)
+    if stats:
+        return out + ({"stages": int(st[0]), "rounds": int(st[1]), "bids": int(st[2]),
+                       "real_bids": int(st[3])},)
     return out
 
 

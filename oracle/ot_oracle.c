@@ -24,6 +24,9 @@
  *                        rows and columns reachable from free rows, exactly
  *                        as KM adjusts them.  Exact mode: scaling factor 1.
  *   oracle_check_certificate   LP-duality certificate of optimality.
+ *   oracle_auction       the auction algorithm with epsilon-scaling (paper,
+ *                        Sec. 2.3.3 and Sec. 4.1 "Auction"), exact for
+ *                        integer costs; readings at the function.
  *
  * Tie-breaks where the paper is silent: rows are rooted in index order, the
  * minimum slack picks the lowest column index, a slack entry is replaced only
@@ -333,4 +336,131 @@ int oracle_check_certificate(const int32_t *C, int64_t ldc, int n, int m,
   }
   free(seen);
   return rc;
+}
+
+/* ------------------------------------------------------------------------
+ * oracle_auction: the auction algorithm with epsilon-scaling (paper,
+ * Sec. 2.3.3 "The auction algorithm" and Sec. 4.1 "Auction": bidders raise
+ * object prices until every bidder holds an object that is within epsilon
+ * of its best; with integral costs the result is exact once epsilon is
+ * below 1/n; epsilon-scaling lowers epsilon in stages, "AuctionScaled").
+ *
+ * Readings (the paper gives no schedule or parallel form):
+ *   - Minimisation form: bidder i values object j at w_ij = C'[i][j] + p_j
+ *     and bids for the object of lowest w (lowest index on ties), raising
+ *     its price by (second-lowest w - lowest w) + eps (by eps when m = 1).
+ *   - Exactness: costs are shifted to start at 0 and multiplied by N + 1
+ *     (N = m bidders after padding), and the last stage runs at eps = 1;
+ *     an eps-optimal assignment of the scaled problem is then within
+ *     N < N + 1 of the scaled optimum, and every assignment's scaled cost is
+ *     a multiple of N + 1, so it is optimal ("epsilon < 1/n").
+ *   - n < m: m - n dummy bidders whose costs are all 0 (a constant row does
+ *     not change which assignment of the real rows is optimal).
+ *   - Parallel (Jacobi) rounds, the parallel bidding the paper mentions:
+ *     every unassigned bidder bids against the prices at the start of the
+ *     round; an object that received bids goes to the highest bid (lowest
+ *     bidder index on ties), takes that bid as its price and releases its
+ *     previous holder.  The outcome of a round does not depend on the
+ *     order in which the bids are computed.
+ *   - Schedule: eps_0 = max(1, R' / 8) with R' = (N + 1) (max C - min C);
+ *     each later stage divides eps by 4 (at least 1), keeps the prices and
+ *     restarts with every bidder unassigned; the stage at eps = 1 is last.
+ *
+ * Outputs row_to_col[n], the final prices p[m] (scaled units) and stats:
+ * [0] stages, [1] rounds, [2] bids (all bidders), [3] bids of real rows.
+ * Returns the cost under C (int64), INT64_MIN on bad sizes, allocation
+ * failure or a scaled range above 2^50.
+ * ---------------------------------------------------------------------- */
+int64_t oracle_auction(const int32_t *C, int64_t ldc, int n, int m, int32_t *row_to_col,
+                       int64_t *prices, int64_t *stats) {
+  if (n < 0 || m < n || (n > 0 && ldc < m)) return INT64_MIN;
+  int64_t st[4] = {0, 0, 0, 0};
+  if (n == 0) {
+    if (prices) memset(prices, 0, sizeof(int64_t) * (size_t)m);
+    if (stats) memcpy(stats, st, sizeof(st));
+    return 0;
+  }
+  const int N = m;
+  int64_t cmin = C[0], cmax = C[0];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < m; ++j) {
+      const int64_t c = C[(int64_t)i * ldc + j];
+      if (c < cmin) cmin = c;
+      if (c > cmax) cmax = c;
+    }
+  const int64_t scale = (int64_t)N + 1;
+  const int64_t range = (cmax - cmin) * scale;
+  if (range > ((int64_t)1 << 50)) return INT64_MIN;
+  int64_t *p = calloc((size_t)N, sizeof(int64_t));
+  int32_t *holder = malloc(sizeof(int32_t) * (size_t)N);  /* object -> bidder or -1 */
+  int32_t *held = malloc(sizeof(int32_t) * (size_t)N);    /* bidder -> object or -1 */
+  int32_t *bid_obj = malloc(sizeof(int32_t) * (size_t)N); /* -1: no bid this round */
+  int64_t *bid_amt = malloc(sizeof(int64_t) * (size_t)N);
+  int32_t *win = malloc(sizeof(int32_t) * (size_t)N);     /* object -> best bidder */
+  if (!p || !holder || !held || !bid_obj || !bid_amt || !win) {
+    free(p); free(holder); free(held); free(bid_obj); free(bid_amt); free(win);
+    return INT64_MIN;
+  }
+  int64_t eps = range / 8;
+  if (eps < 1) eps = 1;
+  for (;;) {
+    ++st[0];
+    for (int k = 0; k < N; ++k) holder[k] = held[k] = -1;
+    for (;;) {
+      /* every unassigned bidder bids against the round-start prices */
+      int bidders = 0;
+      for (int i = 0; i < N; ++i) {
+        bid_obj[i] = -1;
+        if (held[i] >= 0) continue;
+        int j1 = -1;
+        int64_t w1 = OR_INF, w2 = OR_INF;
+        for (int j = 0; j < N; ++j) {
+          const int64_t c = i < n ? (C[(int64_t)i * ldc + j] - cmin) * scale : 0;
+          const int64_t w = c + p[j];
+          if (w < w1) {
+            w2 = w1;
+            w1 = w;
+            j1 = j;
+          } else if (w < w2) {
+            w2 = w;
+          }
+        }
+        if (N == 1) w2 = w1;
+        bid_obj[i] = j1;
+        bid_amt[i] = p[j1] + (w2 - w1) + eps;
+        ++bidders;
+        ++st[2];
+        if (i < n) ++st[3];
+      }
+      if (bidders == 0) break;
+      ++st[1];
+      /* highest bid per object, lowest bidder index among equal bids */
+      for (int j = 0; j < N; ++j) win[j] = -1;
+      for (int i = 0; i < N; ++i) {
+        const int j = bid_obj[i];
+        if (j >= 0 && (win[j] < 0 || bid_amt[i] > bid_amt[win[j]])) win[j] = i;
+      }
+      /* the winner takes the object at its bid; the previous holder is
+         released and bids in the next round */
+      for (int j = 0; j < N; ++j) {
+        if (win[j] < 0) continue;
+        p[j] = bid_amt[win[j]];
+        if (holder[j] >= 0) held[holder[j]] = -1;
+        holder[j] = win[j];
+        held[win[j]] = j;
+      }
+    }
+    if (eps == 1) break;
+    eps /= 4;
+    if (eps < 1) eps = 1;
+  }
+  int64_t cost = 0;
+  for (int i = 0; i < n; ++i) {
+    row_to_col[i] = held[i];
+    cost += C[(int64_t)i * ldc + held[i]];
+  }
+  if (prices) memcpy(prices, p, sizeof(int64_t) * (size_t)N);
+  if (stats) memcpy(stats, st, sizeof(st));
+  free(p); free(holder); free(held); free(bid_obj); free(bid_amt); free(win);
+  return cost;
 }
