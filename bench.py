@@ -8,8 +8,9 @@ vectors (token-embedding-like), solved in one ot_assign_solve_batched call.
 HBM; `e2e` = the same metric through the C-ABI with pinned host buffers
 (host->device copy of every matrix and device->host copy of every result
 inside the timed region).  Side measurements in the same line: the plain
-one-instance-per-launch GPU KM on the same instances, the served
-(continuous batching) p50/p99 latency, and the n = 16384 single solve.
+one-instance-per-launch GPU KM on the same instances, the epsilon-scaling
+auction on the same batch, the served (continuous batching) p50/p99
+latency, and the n = 4096 and n = 16384 single solves.
 
 Under torchrun each rank solves its own 4096 instances (weak scaling, no
 collective on the data path); rank 0 prints the JSON line.
@@ -197,14 +198,15 @@ def run_reference(args):
 
 def measure_single_4096(stream, ot, torch):
     """n = m = 4096 single solves (circle/square shapes and uniform costs):
-    KM on one CTA vs batched KM (routed to the cluster engine), s/solve."""
+    KM on one CTA vs batched KM (routed to the cluster engine) vs the
+    epsilon-scaling auction on one CTA, s/solve."""
     out = {}
     ctx = ot.Context()
     for kind in ("circle-square", "uniform"):
         Cd = torch.from_numpy(W.single_4096(kind)).cuda()
         torch.cuda.synchronize()
         res = {}
-        for name, algo in (("km", ot.OT_KM), ("batched_km", ot.OT_BKM)):
+        for name, algo in (("km", ot.OT_KM), ("batched_km", ot.OT_BKM), ("auction", ot.OT_AUCTION)):
             best = None
             for _ in range(2):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -535,6 +537,25 @@ def main():
         plain = len(sample) / (a0.elapsed_time(a1) / 1000.0)
         line["plain_gpu_km"] = {"value": plain, "unit": UNIT, "sample": f"first {len(sample)} instances, one launch each",
                                 "speedup_of_batched": value / world / plain}
+        # the epsilon-scaling auction (exact) on the same batch, device-resident
+        args_auc = ot.BatchArgs(dC)
+        ot.ot_assign_solve_batched(ctx, args_auc, ot.OT_AUCTION, stream)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(3):
+            ot.ot_assign_solve_batched(ctx, args_auc, ot.OT_AUCTION, stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ast = ot.ot_last_call_stats(ctx)
+        assert (args_auc.status.cpu().numpy() == 0).all()
+        assert (args_auc.cost.cpu().numpy() == args_dev.cost.cpu().numpy()).all(), "auction cost differs from KM"
+        line["auction"] = {"value": 3 * len(dC) / (a0.elapsed_time(a1) / 1000.0), "unit": UNIT,
+                           "ms_per_step": a0.elapsed_time(a1) / 3, "bids": ast["rows_scanned"],
+                           "rounds": ast["steps"], "stages": ast["phases"],
+                           "note": "same 4096 instances, OT_AUCTION, costs equal to KM's"}
+        del args_auc
         cores = host_threads()
         rate, done, dt = cpu_oracle_rate_threads(Cs, args.cpu_seconds, cores)
         rate1, done1, dt1 = cpu_oracle_rate(Cs, args.cpu_seconds / 2)

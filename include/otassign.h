@@ -71,6 +71,17 @@ extern "C" {
 #define OT_AUTO 2   /* per size bucket, whichever of OT_KM / OT_BKM the tuned table
                        names (built-in: KM for m <= 256, batched KM above); both are
                        exact, the optimal assignment and duals returned depend on it */
+#define OT_AUCTION 3  /* the auction algorithm with epsilon-scaling (Sec. 2.3.3 "The
+                       auction algorithm", Sec. 4.1 "Auction"), exact for integer costs:
+                       costs shifted to start at 0 and scaled by m + 1, n < m padded with
+                       zero-cost dummy rows, parallel (Jacobi) bidding rounds, the
+                       highest bid (lowest row on ties) wins, eps_0 = max(1, R'/8) for
+                       the scaled range R', eps /= 4 per stage down to 1.  Returns the
+                       assignment and cost; u and v (when given) receive zeros.  Counters:
+                       steps = bidding rounds, rows_scanned = bids, phases = eps stages,
+                       cost_bytes = 4*m per bid of a real row, init_bytes = 4*n*m (the
+                       range pass).  ot_assign_solve / _stats / _batched only, m <= 4096
+                       (OT_ERR_UNSUPPORTED above). */
 
 /* Per-solve counters, written by ot_assign_solve_stats. */
 typedef struct ot_stats {

@@ -76,6 +76,7 @@ void default_auto(int auto_algo[kNumBuckets]) {
 using namespace ot;
 
 int resolve_algo(const ot_ctx* ctx, int algo, int m) {
+  if (algo == OT_AUCTION) return kAlgoAuction;
   if (algo != OT_AUTO) return algo;
   if (m > kMaxGroupCols) return kAlgoBKM;
   return ctx->auto_algo[bucket_of(m)];
@@ -198,6 +199,21 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
     if (skip[t]) continue;
     const Instance& I = insts[t];
     const int ia = resolve_algo(ctx, algo, I.m);
+    if (ia == kAlgoAuction) {
+      // the auction engine: one CTA per instance, sized by m
+      if (I.m > kMaxGroupCols || auction_smem_bytes(I.m) > group_smem_limit()) {
+        if (unsupported) unsupported->push_back(t);
+        continue;
+      }
+      const int th = auction_threads(I.m);
+      Bucket& b = buckets[ia * 64 + th / 32];
+      b.shape = th;
+      b.algo = ia;
+      b.nmax = std::max(b.nmax, I.n);
+      b.mmax = std::max(b.mmax, I.m);
+      b.idx.push_back(t);
+      continue;
+    }
     int sh = ctx->table[ia][bucket_of(I.m)];
     if (route_wide && ia == kAlgoBKM && I.m > kClusterRouteCols && !ctx->tuned[ia][bucket_of(I.m)]) sh = kLargeEngine;
     if (sh == kLargeEngine) {  // bucket routed to the cluster engine
@@ -230,7 +246,8 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
   if (pack_on && !buckets.empty()) {
     size_t nrows = 0, nelem = 0;
     for (auto& kv : buckets)
-      for (int t : kv.second.idx) { nrows += insts[t].n; nelem += size_t(insts[t].n) * insts[t].m; }
+      if (kv.second.algo != kAlgoAuction)
+        for (int t : kv.second.idx) { nrows += insts[t].n; nelem += size_t(insts[t].n) * insts[t].m; }
     const size_t b_pok = al256(sizeof(int32_t) * k), b_roff = al256(sizeof(int32_t) * nrows);
     const int genp = slot.d_pack.generation;
     if (slot.d_pack.reserve(b_pok + b_roff + al256(2 * nelem)) == OT_OK) {
@@ -242,13 +259,14 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
       size_t orow = 0, oel = 0;
       for (auto& kv : buckets)
         for (int t : kv.second.idx) {
+          if (kv.second.algo == kAlgoAuction) continue;
           insts[t].pok = pok + t;
           insts[t].roff = roff + orow;
           insts[t].P = P + oel;
           orow += insts[t].n;
           oel += size_t(insts[t].n) * insts[t].m;
         }
-      any_pack = true;
+      any_pack = nelem > 0;
     }
   }
   // a shape may serve several m-buckets; keep the smem bound feasible
@@ -312,6 +330,12 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
     slot.meta_valid = true;
   }
 
+  auto launch_bucket = [&](const Bucket& b, int bi, cudaStream_t s) -> cudaError_t {
+    if (b.algo == kAlgoAuction)
+      return launch_auction(b.shape, dinst, dorder + offs[bi], int(b.idx.size()), dwork + bi, b.mmax, s);
+    return launch_group(group_shape(b.shape), b.algo, dinst, dorder + offs[bi], int(b.idx.size()), dwork + bi,
+                        b.nmax, b.mmax, max_ctas_env(), s);
+  };
   auto enqueue = [&](cudaStream_t s) -> cudaError_t {
     cudaError_t e = cudaMemsetAsync(dwork, 0, work_bytes, s);
     if (e != cudaSuccess) return e;
@@ -320,8 +344,7 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
       int bi = 0;
       for (auto& kv : buckets) {
         Bucket& b = kv.second;
-        e = launch_group(group_shape(b.shape), b.algo, dinst, dorder + offs[bi], int(b.idx.size()),
-                         dwork + bi, b.nmax, b.mmax, max_ctas_env(), s);
+        e = launch_bucket(b, bi, s);
         if (e != cudaSuccess) return e;
         ++bi;
       }
@@ -333,8 +356,7 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
       Bucket& b = kv.second;
       cudaStream_t bs = ctx->bstreams[bi % kForkStreams];
       if ((e = cudaStreamWaitEvent(bs, ctx->fork_ev, 0)) != cudaSuccess) return e;
-      e = launch_group(group_shape(b.shape), b.algo, dinst, dorder + offs[bi], int(b.idx.size()),
-                       dwork + bi, b.nmax, b.mmax, max_ctas_env(), bs);
+      e = launch_bucket(b, bi, bs);
       if (e != cudaSuccess) return e;
       ++bi;
     }
@@ -394,7 +416,8 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
                       const int32_t* n, const int32_t* m, int algo, int32_t* const* r2c,
                       int64_t* cost, int64_t* const* u, int64_t* const* v, int32_t* status,
                       cudaStream_t stream, ot_stats* stats_out, bool route_wide) {
-  if (algo != OT_KM && algo != OT_BKM && algo != OT_AUTO) return ctx_fail(ctx, OT_ERR_ARG, "bad algo");
+  if (algo != OT_KM && algo != OT_BKM && algo != OT_AUTO && algo != OT_AUCTION)
+    return ctx_fail(ctx, OT_ERR_ARG, "bad algo");
   if (k < 0) return ctx_fail(ctx, OT_ERR_ARG, "k < 0");
   if (k == 0) return OT_OK;
   if (!C || !ldc || !n || !m || !r2c || !cost) return ctx_fail(ctx, OT_ERR_ARG, "null array");
@@ -437,7 +460,11 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
     ctx->last_skip = skip;
     // instances wider than a group: the cluster engine, one at a time
     for (int t : unsup) {
-      if (insts[t].m > large_max_cols()) { st[t] = OT_ERR_UNSUPPORTED; ctx->last_skip[t] = 1; continue; }
+      if (insts[t].m > large_max_cols() || algo == OT_AUCTION) {
+        st[t] = OT_ERR_UNSUPPORTED;
+        ctx->last_skip[t] = 1;
+        continue;
+      }
       const int rc = solve_large(ctx, insts[t], resolve_algo(ctx, algo, insts[t].m), stream, nullptr);
       if (rc == OT_ERR_TIMEOUT || rc == OT_ERR_UNSUPPORTED) { st[t] = rc; continue; }
       if (rc != OT_OK) return rc;
@@ -543,7 +570,7 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
   ctx->last_skip = skip;
   std::vector<int> still;
   for (int t : unsup) {
-    if (insts[t].m > large_max_cols()) { still.push_back(t); continue; }
+    if (insts[t].m > large_max_cols() || algo == OT_AUCTION) { still.push_back(t); continue; }
     const int rc = solve_large(ctx, insts[t], resolve_algo(ctx, algo, insts[t].m), stream, nullptr);
     if (rc == OT_ERR_TIMEOUT || rc == OT_ERR_UNSUPPORTED) { st[t] = rc; skip[t] = 1; continue; }
     if (rc != OT_OK) return rc;

@@ -30,7 +30,7 @@
 
 namespace ot {
 
-enum { kAlgoKM = 0, kAlgoBKM = 1 };
+enum { kAlgoKM = 0, kAlgoBKM = 1, kAlgoAuction = 2 };  // auction: ot_auction.cu
 
 // status codes written by the device (match OT_ERR_* in otassign.h)
 enum { kDevOk = 0, kDevStepLimit = -4 };

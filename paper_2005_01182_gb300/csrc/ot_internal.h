@@ -57,4 +57,11 @@ GroupShape group_shape(int idx);
 size_t group_smem_bytes(GroupShape shape, int algo, int nmax, int mmax);
 size_t group_smem_limit();
 
+// Auction engine (ot_auction.cu): one CTA of auction_threads(m) threads
+// per instance; `num` instances listed in `order`, pulled from `work`.
+int auction_threads(int m);
+size_t auction_smem_bytes(int mmax);
+cudaError_t launch_auction(int threads, const Instance* insts, const int32_t* order, int num, int* work,
+                           int mmax, cudaStream_t stream);
+
 }  // namespace ot

@@ -32,6 +32,7 @@ OT_ERR_TICKET = -8
 OT_KM = 0
 OT_BKM = 1
 OT_AUTO = 2
+OT_AUCTION = 3
 
 _lib = None
 
