@@ -20,6 +20,9 @@ What each function follows in the paper:
     "Auction"), exact for integer costs by scaling them by N + 1 and
     finishing at epsilon = 1.
 
+``oracle.sinkhorn`` (numpy, float64) holds the log-domain Sinkhorn of
+Sec. 2.2.1, pinned in ``tests/test_oracle_sinkhorn.py``.
+
 Parity is pinned for every function (brute force over permutations, closed
 forms, scipy's ``linear_sum_assignment``, the certificate); see
 ``tests/test_oracle.py``.  bKM's intermediate round structure (how many
