@@ -150,6 +150,31 @@ int ot_transport_solve(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, in
                        const int32_t* supply, const int32_t* demand, int32_t algo, int64_t* cost,
                        int32_t* flow, void* stream);
 
+/* Entropic optimal transport by log-domain Sinkhorn (Sec. 2.2 "Matrix
+ * Scaling", Sec. 2.2.1 "Sinkhorn"; configuration of Sec. 4.1 "Sinkhorn"):
+ * min <X, C> - h(X)/eta over X 1 = r, X^T 1 = c, solved as
+ * X_ij = exp(f_i + g_j - eta C_ij).  Starting from f = g = 0, each
+ * iteration scales every row (f_i = log r_i - LSE_j(g_j - eta C_ij)) and
+ * then every column (g_j = log c_j - LSE_i(f_i - eta C_ij)).  The first
+ * iterate whose residue sum_i |r_i - (X 1)_i| is at most eps_rel * sum(r)
+ * is returned (the paper uses eps_rel = 1e-3 and no rounding; the column
+ * sums are exact after the column scaling); with eps_rel <= 0, or when
+ * max_iter iterations do not reach it, iterate max_iter is returned.
+ *   C: device pointer, n x m int32 (ldc >= m); r (n), c (m): host arrays of
+ *   positive supplies and demands with equal totals, or NULL for r = 1 and
+ *   c = n/m.  f (n), g (m): float32 outputs (host or device, may be NULL);
+ *   *cost = <C, X> (double), *residue, *iterations: host pointers
+ *   (residue and iterations may be NULL).
+ * Arithmetic is float32 for the exponent arguments, exponentials and sums
+ * and double for the residue and cost accumulators.  Each iteration reads
+ * C twice (a row pass and a column pass).  Synchronous.  OT_ERR_ARG for
+ * n, m < 1, eta <= 0, max_iter < 1, non-positive or unbalanced marginals,
+ * or a host C. */
+int ot_sinkhorn_solve(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int32_t m,
+                      const double* r, const double* c, double eta, double eps_rel,
+                      int32_t max_iter, float* f, float* g, double* cost, double* residue,
+                      int32_t* iterations, void* stream);
+
 /* Synchronise the context's stream and return the counters of the most
  * recent ot_assign_solve / ot_assign_solve_batched call on device pointers,
  * summed over its instances; reserved[0] receives the number of kernel

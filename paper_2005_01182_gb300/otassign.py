@@ -98,6 +98,9 @@ def load(path: str | None = None):
                                                            pp, vp, pp, pp, vp, vp]),
         "ot_assign_solve_scaled": (ctypes.c_int, [vp, vp, i64, i32, i32, i32, vp, vp, vp, vp]),
         "ot_transport_solve": (ctypes.c_int, [vp, vp, i64, i32, i32, vp, vp, i32, vp, vp, vp]),
+        "ot_sinkhorn_solve": (ctypes.c_int, [vp, vp, i64, i32, i32, vp, vp, ctypes.c_double, ctypes.c_double,
+                                             i32, vp, vp, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), vp]),
         "ot_version": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -280,6 +283,26 @@ def ot_transport_solve(ctx: Context, C: torch.Tensor, supply, demand, algo: int 
                                     _stream_handle(stream))
     ctx._raise(rc, "ot_transport_solve")
     return flow, int(c.item())
+
+
+def ot_sinkhorn_solve(ctx: Context, C: torch.Tensor, eta: float, eps_rel: float = 1e-3, max_iter: int = 1000,
+                      r=None, c=None, stream=None):
+    """Log-domain Sinkhorn on a device cost matrix.  Returns (f, g) float32
+    on C's device and (cost, residue, iterations)."""
+    import numpy as np
+    n, m, ldc = _check_cost(C)
+    f = torch.empty(n, dtype=torch.float32, device=C.device)
+    g = torch.empty(m, dtype=torch.float32, device=C.device)
+    rr = None if r is None else np.ascontiguousarray(r, dtype=np.float64)
+    cc = None if c is None else np.ascontiguousarray(c, dtype=np.float64)
+    cost, res, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    rc = ctx.lib.ot_sinkhorn_solve(ctx.h, _ptr(C), ldc, n, m,
+                                   None if rr is None else ctypes.c_void_p(rr.ctypes.data),
+                                   None if cc is None else ctypes.c_void_p(cc.ctypes.data),
+                                   float(eta), float(eps_rel), int(max_iter), _ptr(f), _ptr(g),
+                                   ctypes.byref(cost), ctypes.byref(res), ctypes.byref(it), _stream_handle(stream))
+    ctx._raise(rc, "ot_sinkhorn_solve")
+    return f, g, (cost.value, res.value, it.value)
 
 
 def ot_last_call_stats(ctx: Context) -> dict:
