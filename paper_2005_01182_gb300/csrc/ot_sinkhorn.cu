@@ -30,8 +30,29 @@
 #include "otassign.h"
 #include "ot_ctx.h"
 
+// Launch shape of the two passes (compile-time; the defaults are the ones
+// measured best on GB300 for n = m = 16384).
+#ifndef OT_SK_ROW_UNROLL
+#define OT_SK_ROW_UNROLL 4
+#endif
+#ifndef OT_SK_ROW_MINB
+#define OT_SK_ROW_MINB 1
+#endif
+#ifndef OT_SK_COL_T
+#define OT_SK_COL_T 128
+#endif
+#ifndef OT_SK_COL_CTAS
+#define OT_SK_COL_CTAS 8
+#endif
+#ifndef OT_SK_COL_UNROLL
+#define OT_SK_COL_UNROLL 8
+#endif
+
 namespace ot {
 namespace {
+
+constexpr int kRowUnroll = OT_SK_ROW_UNROLL;
+constexpr int kColUnroll = OT_SK_COL_UNROLL;
 
 struct SkState {
   int done;        // set when the returned iterate is final
@@ -48,19 +69,6 @@ struct Lse {
   float s;  // sum of exp(x - m)
   float w;  // sum of C * exp(x - m) (row pass only)
 };
-
-__device__ __forceinline__ void lse_add(Lse& a, float x, float c) {
-  if (x > a.m) {
-    const float sc = __expf(a.m - x);  // 0 when a.m = -inf
-    a.s = a.s * sc + 1.0f;
-    a.w = a.w * sc + c;
-    a.m = x;
-  } else {
-    const float e = __expf(x - a.m);
-    a.s += e;
-    a.w += c * e;
-  }
-}
 
 __device__ __forceinline__ Lse lse_merge(Lse a, Lse b) {
   if (b.s == 0.0f) return a;
@@ -88,10 +96,42 @@ __device__ __forceinline__ Lse warp_lse(Lse a) {
   return a;
 }
 
+// Fold N values held in registers into a running log-sum-exp: one maximum
+// over the chunk, one rescale of the running sums, then N independent
+// exponentials (no data-dependent branch; -inf entries contribute 0).  The
+// chunk must hold at least one finite value.
+template <int N, bool W>
+__device__ __forceinline__ void lse_chunk(Lse& a, const float (&x)[N], const float (&c)[N]) {
+  float cm = x[0];
+#pragma unroll
+  for (int k = 1; k < N; ++k) cm = fmaxf(cm, x[k]);
+  const float mn = fmaxf(a.m, cm);
+  const float sc = __expf(a.m - mn);  // 0 when a.m = -inf
+  float s0 = 0.0f, s1 = 0.0f, w0 = 0.0f, w1 = 0.0f;
+#pragma unroll
+  for (int k = 0; k < N; k += 2) {
+    const float e0 = __expf(x[k] - mn);
+    s0 += e0;
+    if (W) w0 = fmaf(c[k], e0, w0);
+    if (k + 1 < N) {
+      const float e1 = __expf(x[k + 1] - mn);
+      s1 += e1;
+      if (W) w1 = fmaf(c[k + 1], e1, w1);
+    }
+  }
+  a.s = fmaf(a.s, sc, s0 + s1);
+  if (W) a.w = fmaf(a.w, sc, w0 + w1);
+  a.m = mn;
+}
+
 // Row pass of iteration k: f_new = log r - LSE_j(g - eta C); with `check`,
-// also the residue and cost of the iterate (f_old, g) into acc[k & 1].
+// also the residue and cost of the iterate (f_old, g) into acc[k & 1].  A
+// warp takes two adjacent rows (they share the loads of g); each lane keeps
+// kRowChunk 16-byte loads of both rows in flight before it folds them.
+constexpr int kRowChunk = 4;
+
 template <bool VEC>
-__global__ void __launch_bounds__(256) sk_row_pass(const int32_t* __restrict__ C, long long ldc, int n, int m,
+__global__ void __launch_bounds__(256, OT_SK_ROW_MINB) sk_row_pass(const int32_t* __restrict__ C, long long ldc, int n, int m,
                                                    float eta, const float* __restrict__ g,
                                                    const float* __restrict__ f_old, float* __restrict__ f_new,
                                                    const float* __restrict__ logr, const double* __restrict__ r,
@@ -101,43 +141,88 @@ __global__ void __launch_bounds__(256) sk_row_pass(const int32_t* __restrict__ C
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int warps = gridDim.x * 8;
   double res = 0.0, cost = 0.0;
-  for (int i = blockIdx.x * 8 + wid; i < n; i += warps) {
-    const int32_t* row = C + (long long)i * ldc;
-    Lse a{-INFINITY, 0.0f, 0.0f};
+  for (int i = 2 * (blockIdx.x * 8 + wid); i < n; i += 2 * warps) {
+    const bool two = i + 1 < n;
+    const int32_t* row0 = C + (long long)i * ldc;
+    const int32_t* row1 = two ? row0 + ldc : row0;
+    Lse a0{-INFINITY, 0.0f, 0.0f}, a1{-INFINITY, 0.0f, 0.0f};
     if (VEC) {
-      const int4* row4 = reinterpret_cast<const int4*>(row);
+      const int nq = m >> 2;
+      const int4* r0 = reinterpret_cast<const int4*>(row0);
+      const int4* r1 = reinterpret_cast<const int4*>(row1);
       const float4* g4 = reinterpret_cast<const float4*>(g);
-#pragma unroll 2
-      for (int q = lane; q < (m >> 2); q += 32) {
-        const int4 c = __ldg(row4 + q);
-        const float4 gv = __ldg(g4 + q);
-        lse_add(a, fmaf(-eta, float(c.x), gv.x), float(c.x));
-        lse_add(a, fmaf(-eta, float(c.y), gv.y), float(c.y));
-        lse_add(a, fmaf(-eta, float(c.z), gv.z), float(c.z));
-        lse_add(a, fmaf(-eta, float(c.w), gv.w), float(c.w));
+      for (int q0 = lane; q0 < nq; q0 += 32 * kRowChunk) {
+        int4 c0[kRowChunk], c1[kRowChunk];
+        float4 gv[kRowChunk];
+#pragma unroll
+        for (int u = 0; u < kRowChunk; ++u) {
+          const int q = q0 + 32 * u;
+          if (q < nq) {
+            c0[u] = __ldg(r0 + q);
+            c1[u] = __ldg(r1 + q);
+            gv[u] = __ldg(g4 + q);
+          } else {
+            c0[u] = c1[u] = make_int4(0, 0, 0, 0);
+            gv[u] = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+          }
+        }
+        float x[4 * kRowChunk], cf[4 * kRowChunk];
+#pragma unroll
+        for (int u = 0; u < kRowChunk; ++u) {
+          cf[4 * u + 0] = float(c0[u].x); cf[4 * u + 1] = float(c0[u].y);
+          cf[4 * u + 2] = float(c0[u].z); cf[4 * u + 3] = float(c0[u].w);
+          x[4 * u + 0] = fmaf(-eta, cf[4 * u + 0], gv[u].x); x[4 * u + 1] = fmaf(-eta, cf[4 * u + 1], gv[u].y);
+          x[4 * u + 2] = fmaf(-eta, cf[4 * u + 2], gv[u].z); x[4 * u + 3] = fmaf(-eta, cf[4 * u + 3], gv[u].w);
+        }
+        lse_chunk<4 * kRowChunk, true>(a0, x, cf);
+#pragma unroll
+        for (int u = 0; u < kRowChunk; ++u) {
+          cf[4 * u + 0] = float(c1[u].x); cf[4 * u + 1] = float(c1[u].y);
+          cf[4 * u + 2] = float(c1[u].z); cf[4 * u + 3] = float(c1[u].w);
+          x[4 * u + 0] = fmaf(-eta, cf[4 * u + 0], gv[u].x); x[4 * u + 1] = fmaf(-eta, cf[4 * u + 1], gv[u].y);
+          x[4 * u + 2] = fmaf(-eta, cf[4 * u + 2], gv[u].z); x[4 * u + 3] = fmaf(-eta, cf[4 * u + 3], gv[u].w);
+        }
+        lse_chunk<4 * kRowChunk, true>(a1, x, cf);
       }
       for (int j = (m & ~3) + lane; j < m; j += 32) {
-        const float c = float(row[j]);
-        lse_add(a, fmaf(-eta, c, __ldg(g + j)), c);
+        const float gj = __ldg(g + j);
+        float x0[1], x1[1], cc0[1], cc1[1];
+        cc0[0] = float(row0[j]);
+        cc1[0] = float(row1[j]);
+        x0[0] = fmaf(-eta, cc0[0], gj);
+        x1[0] = fmaf(-eta, cc1[0], gj);
+        lse_chunk<1, true>(a0, x0, cc0);
+        lse_chunk<1, true>(a1, x1, cc1);
       }
     } else {
       for (int j = lane; j < m; j += 32) {
-        const float c = float(__ldg(row + j));
-        lse_add(a, fmaf(-eta, c, __ldg(g + j)), c);
+        const float gj = __ldg(g + j);
+        float x0[1], x1[1], cc0[1], cc1[1];
+        cc0[0] = float(__ldg(row0 + j));
+        cc1[0] = float(__ldg(row1 + j));
+        x0[0] = fmaf(-eta, cc0[0], gj);
+        x1[0] = fmaf(-eta, cc1[0], gj);
+        lse_chunk<1, true>(a0, x0, cc0);
+        lse_chunk<1, true>(a1, x1, cc1);
       }
     }
-    a = warp_lse(a);
-    const float L = a.m + logf(a.s);
-    if (lane == 0) {
-      f_new[i] = (logr ? logr[i] : 0.0f) - L;
+    a0 = warp_lse(a0);
+    a1 = warp_lse(a1);
+    if (lane < 2 && (lane == 0 || two)) {
+      const int ii = i + lane;
+      const Lse& a = lane == 0 ? a0 : a1;
+      const float L = a.m + logf(a.s);
+      f_new[ii] = (logr ? logr[ii] : 0.0f) - L;
       if (check) {
-        const double fo = double(f_old[i]);
-        res += fabs((r ? r[i] : 1.0) - exp(fo + double(L)));
+        const double fo = double(f_old[ii]);
+        res += fabs((r ? r[ii] : 1.0) - exp(fo + double(L)));
         cost += exp(fo + double(a.m)) * double(a.w);
       }
     }
   }
   if (!check) return;
+  res += __shfl_down_sync(0xffffffffu, res, 1);
+  cost += __shfl_down_sync(0xffffffffu, cost, 1);
   if (lane == 0) {
     red[0][wid] = res;
     red[1][wid] = cost;
@@ -158,7 +243,10 @@ __global__ void __launch_bounds__(256) sk_row_pass(const int32_t* __restrict__ C
 // (whose residue the row pass of iteration k accumulated): when it passes, or
 // when `final_k` > 0 asks for iterate final_k to be returned as it is, the
 // state is recorded and nothing else happens.  Otherwise partial column
-// LSEs over this CTA's rows; the last CTA of a column tile merges them into g.
+// LSEs over this CTA's rows, kColChunk rows of 16-byte loads in flight per
+// thread; the last CTA of a column tile merges the partials into g.
+constexpr int kColChunk = kColUnroll;
+
 template <int T, bool VEC>
 __global__ void __launch_bounds__(T) sk_col_pass(const int32_t* __restrict__ C, long long ldc, int n, int m,
                                                  float eta, const float* __restrict__ f, float* __restrict__ g,
@@ -189,24 +277,41 @@ __global__ void __launch_bounds__(T) sk_col_pass(const int32_t* __restrict__ C, 
 #pragma unroll
   for (int q = 0; q < 4; ++q) a[q] = Lse{-INFINITY, 0.0f, 0.0f};
   if (j0 < m) {
-    if (VEC && j0 + 3 < m) {
-#pragma unroll 4
-      for (int i = i0; i < i1; ++i) {
-        const int4 c = __ldg(reinterpret_cast<const int4*>(C + (long long)i * ldc + j0));
-        const float fi = __ldg(f + i);
-        lse_add(a[0], fmaf(-eta, float(c.x), fi), 0.0f);
-        lse_add(a[1], fmaf(-eta, float(c.y), fi), 0.0f);
-        lse_add(a[2], fmaf(-eta, float(c.z), fi), 0.0f);
-        lse_add(a[3], fmaf(-eta, float(c.w), fi), 0.0f);
-      }
-    } else {
-      for (int i = i0; i < i1; ++i) {
-        const int32_t* row = C + (long long)i * ldc;
-        const float fi = __ldg(f + i);
+    const bool full = VEC && j0 + 3 < m;
+    for (int ib = i0; ib < i1; ib += kColChunk) {
+      // rows past the block end are loaded from the last row (a valid
+      // address, no branch around the loads) and weighted out by f = -inf
+      int4 c[kColChunk];
+      float fi[kColChunk];
+      if (full) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (j0 + q < m) lse_add(a[q], fmaf(-eta, float(__ldg(row + j0 + q)), fi), 0.0f);
+        for (int u = 0; u < kColChunk; ++u)
+          c[u] = __ldg(reinterpret_cast<const int4*>(C + (long long)min(ib + u, i1 - 1) * ldc + j0));
+      } else {
+#pragma unroll
+        for (int u = 0; u < kColChunk; ++u) {
+          const int32_t* p = C + (long long)min(ib + u, i1 - 1) * ldc + j0;
+          c[u].x = __ldg(p);
+          c[u].y = j0 + 1 < m ? __ldg(p + 1) : 0;
+          c[u].z = j0 + 2 < m ? __ldg(p + 2) : 0;
+          c[u].w = j0 + 3 < m ? __ldg(p + 3) : 0;
+        }
       }
+#pragma unroll
+      for (int u = 0; u < kColChunk; ++u) fi[u] = ib + u < i1 ? __ldg(f + ib + u) : -INFINITY;
+      float x[kColChunk], cz[kColChunk];
+#pragma unroll
+      for (int u = 0; u < kColChunk; ++u) { x[u] = fmaf(-eta, float(c[u].x), fi[u]); cz[u] = 0.0f; }
+      lse_chunk<kColChunk, false>(a[0], x, cz);
+#pragma unroll
+      for (int u = 0; u < kColChunk; ++u) x[u] = fmaf(-eta, float(c[u].y), fi[u]);
+      lse_chunk<kColChunk, false>(a[1], x, cz);
+#pragma unroll
+      for (int u = 0; u < kColChunk; ++u) x[u] = fmaf(-eta, float(c[u].z), fi[u]);
+      lse_chunk<kColChunk, false>(a[2], x, cz);
+#pragma unroll
+      for (int u = 0; u < kColChunk; ++u) x[u] = fmaf(-eta, float(c[u].w), fi[u]);
+      lse_chunk<kColChunk, false>(a[3], x, cz);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -220,25 +325,33 @@ __global__ void __launch_bounds__(T) sk_col_pass(const int32_t* __restrict__ C, 
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int q = 0; q < 4; ++q) {
-    const int j = j0 + q;
-    if (j >= m) continue;
-    Lse s{-INFINITY, 0.0f, 0.0f};
-    // eight partials in flight per round: the merge is bound by L2 latency
-    for (int b0 = 0; b0 < nrb; b0 += 8) {
-      float2 p[8];
+  // the merge is bound by L2 latency: 4 partials of each of the thread's 4
+  // columns in flight per round
+  Lse s[4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        p[u] = b0 + u < nrb ? __ldcg(part + (long long)(b0 + u) * m + j) : make_float2(-INFINITY, 0.0f);
+  for (int q = 0; q < 4; ++q) s[q] = Lse{-INFINITY, 0.0f, 0.0f};
+  if (j0 < m) {
+    for (int b0 = 0; b0 < nrb; b0 += 4) {
+      float2 p[4][4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) s = lse_merge(s, Lse{p[u].x, p[u].y, 0.0f});
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          p[u][q] = (b0 + u < nrb && j0 + q < m) ? __ldcg(part + (long long)(b0 + u) * m + j0 + q)
+                                                 : make_float2(-INFINITY, 0.0f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s[q] = lse_merge(s[q], Lse{p[u][q].x, p[u][q].y, 0.0f});
     }
-    g[j] = (logc ? logc[j] : 0.0f) - (s.m + logf(s.s));
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (j0 + q < m) g[j0 + q] = (logc ? logc[j0 + q] : 0.0f) - (s[q].m + logf(s[q].s));
   }
   if (threadIdx.x == 0) tile_count[blockIdx.x] = 0;
 }
 
-constexpr int kColT = 128;
+constexpr int kColT = OT_SK_COL_T;
 
 }  // namespace
 }  // namespace ot
@@ -279,11 +392,11 @@ extern "C" int ot_sinkhorn_solve(ot_ctx* ctx, const int32_t* C, int64_t ldc, int
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
 
-  // column pass geometry: tiles of 4*T columns, enough row blocks to fill
-  // the GPU, but at least 64 rows per block (the merge of the partials is
-  // latency-bound in their number)
+  // column pass geometry: tiles of 4*T columns and enough row blocks for
+  // OT_SK_COL_CTAS CTAs per SM (loads in flight), but at least 64 rows per block (the
+  // merge of the partials is latency-bound in their number)
   const int tiles = (m + 4 * kColT - 1) / (4 * kColT);
-  int nrb = std::max(1, std::min((n + 63) / 64, (4 * sms + tiles - 1) / tiles));
+  int nrb = std::max(1, std::min((n + 63) / 64, (OT_SK_COL_CTAS * sms + tiles - 1) / tiles));
   const int rows_per_block = (n + nrb - 1) / nrb;
   nrb = (n + rows_per_block - 1) / rows_per_block;
 
@@ -317,7 +430,7 @@ extern "C" int ot_sinkhorn_solve(ot_ctx* ctx, const int32_t* C, int64_t ldc, int
 
   const bool vec = (ldc % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
   const double threshold = eps_rel > 0.0 ? eps_rel * tr : -1.0;
-  const int row_grid = std::max(1, std::min((n + 7) / 8, 8 * sms));
+  const int row_grid = std::max(1, std::min((n + 15) / 16, 8 * sms));
   const dim3 col_grid(tiles, nrb);
   // host copy of the state, polled every `chunk` iterations
   SkState h{};
