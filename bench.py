@@ -10,7 +10,9 @@ HBM; `e2e` = the same metric through the C-ABI with pinned host buffers
 inside the timed region).  Side measurements in the same line: the plain
 one-instance-per-launch GPU KM on the same instances, the epsilon-scaling
 auction on the same batch, the served (continuous batching) p50/p99
-latency, and the n = 4096 and n = 16384 single solves.
+latency, the n = 4096 and n = 16384 single solves, and log-domain Sinkhorn
+(per-iteration bandwidth at n = 16384; the paper's 1.1-approximation
+protocol at n = 4096).
 
 Under torchrun each rank solves its own 4096 instances (weak scaling, no
 collective on the data path); rank 0 prints the JSON line.
@@ -36,6 +38,36 @@ from paper_2005_01182_gb300 import workloads as W  # noqa: E402
 
 METRIC = "assignment solves/s (4096-instance batch, n~U{32..256}, exact)"
 UNIT = "solves/s"
+
+
+KERNEL_SOURCES = ["ot_group.cuh", "ot_group_km.cu", "ot_group_bkm.cu", "ot_group_launch.inc", "ot_shapes.h",
+                  "ot_internal.h", "ot_pack.cu"]
+
+
+def kernel_source_hash() -> str:
+    """sha256 over the sources that define the group-engine kernels."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2005_01182_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    it was taken on the kernel sources as they are now (else None).  Lines:
+    `traffic <kernel> <bytes per launch> source <sha256>`."""
+    p = os.path.join(ROOT, "profiles", "batch4096_embed_traffic.md")
+    if not os.path.exists(p):
+        return None
+    digest = kernel_source_hash()
+    for line in open(p):
+        tok = line.strip().strip("`").split()
+        if len(tok) >= 5 and tok[0] == "traffic" and tok[-2] == "source":
+            name = " ".join(tok[1:-3])
+            if name == kernel and tok[-1] == digest:
+                return int(tok[-3])
+    return None
 
 
 def _peaks():
@@ -227,6 +259,7 @@ def measure_single_16384(ctx, stream, ot, torch):
     batched KM solve time and effective cost-matrix bandwidth."""
     C = W.single_16384()
     Cd = torch.from_numpy(C).cuda()
+    C_shape = C.shape
     del C
     torch.cuda.synchronize()
     peak, kind = _peaks()
@@ -255,14 +288,62 @@ def measure_single_16384(ctx, stream, ot, torch):
         torch.cuda.synchronize()
         scaled[str(sc)] = {"s_per_solve": e0.elapsed_time(e1) / 1000.0, "cost": int(c2.item()),
                            "ratio_to_opt": int(c2.item()) / cost, "bound": bnd, "bound_ratio": 1 + bnd / cost}
+    # log-domain Sinkhorn on the same matrix: the cost of one iteration (a row
+    # pass and a column pass, each reading the 1 GiB matrix once), from the
+    # difference of a 12- and a 2-iteration run
+    sk_t = {}
+    for K in (2, 12):
+        ot.ot_sinkhorn_solve(ctx, Cd, 2.0, eps_rel=0.0, max_iter=K, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ot.ot_sinkhorn_solve(ctx, Cd, 2.0, eps_rel=0.0, max_iter=K, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sk_t[K] = e0.elapsed_time(e1) / 1000.0
+    per_it = (sk_t[12] - sk_t[2]) / 10
+    sk_bytes = 2 * 4 * C_shape[0] * C_shape[1]
+    sinkhorn = {"s_per_iteration": per_it, "bytes_per_iteration": sk_bytes,
+                "achieved_gbs": sk_bytes / per_it / 1e9, "hbm_frac": sk_bytes / per_it / 1e9 / peak,
+                "hbm_frac_vs_8tbs": sk_bytes / per_it / 1e9 / 8000.0, "eta": 2.0,
+                "note": "log-domain Sinkhorn, fixed iterations; (t(12) - t(2)) / 10"}
     del Cd
     torch.cuda.empty_cache()
-    return {"algo": "batched KM", "s_per_solve": t, "solves_per_s": 1.0 / t, "cost": cost,
+    return {"algo": "batched KM", "s_per_solve": t, "solves_per_s": 1.0 / t, "cost": cost, "sinkhorn": sinkhorn,
             "algorithmic_bytes": alg, "achieved_gbs": alg / t / 1e9,
             "hbm_frac": alg / t / 1e9 / peak, "peak_gbs": peak, "peak_kind": kind,
             "hbm_frac_vs_8tbs": alg / t / 1e9 / 8000.0,
             "steps": st["steps"], "phases": st["phases"], "rows_scanned": st["rows_scanned"],
             "scaled_batched_km": scaled}
+
+
+def measure_sinkhorn_4096(stream, ot, torch):
+    """The paper's Sinkhorn protocol (Sec. 4.1) on the n = 4096 circle/square
+    instance: epsilon = 0.1% of the total demand, no rounding, and the
+    smallest eta of a geometric grid whose cost is within 110% of the exact
+    optimum (batched KM here).  Time to convergence per eta."""
+    ctx = ot.Context()
+    Cd = torch.from_numpy(W.single_4096("circle-square")).cuda()
+    _, c, _, _ = ot.ot_assign_solve(ctx, Cd, ot.OT_BKM, stream)
+    torch.cuda.synchronize()
+    opt = int(c.item())
+    tried = []
+    chosen = None
+    for eta in (1e-3, 3e-3, 1e-2, 3e-2, 0.1, 0.3, 1.0):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f, g, (cost, res, it) = ot.ot_sinkhorn_solve(ctx, Cd, eta, eps_rel=1e-3, max_iter=20000, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rec = {"eta": eta, "iterations": it, "s": e0.elapsed_time(e1) / 1000.0, "cost_over_opt": cost / opt,
+               "residue_over_total": res / 4096}
+        tried.append(rec)
+        if cost <= 1.1 * opt:
+            chosen = rec
+            break
+    ctx.close()
+    del Cd
+    torch.cuda.empty_cache()
+    return {"opt": opt, "epsilon_rel": 1e-3, "chosen": chosen, "tried": tried}
 
 
 def measure_served(ctx_unused, stream, ot, torch, dev, args):
@@ -459,6 +540,18 @@ def main():
     # correctness spot check of the timed results (cost must be finite/status ok)
     assert (args_dev.status.cpu().numpy() == 0).all(), "device status error"
 
+    # the dominant kernel of a step, timed by the CUDA events the library
+    # records around every bucket kernel on the stream it launches on
+    kern = []
+    for _ in range(5):
+        ot.ot_assign_solve_batched(ctx, args_dev, algo, stream)
+        kern.append(ot.ot_last_call_launches(ctx))
+    dom_idx = max(range(len(kern[0])), key=lambda b: sum(k[b]["ms"] for k in kern))
+    dom = kern[0][dom_idx]
+    dom_ms = float(np.mean([k[dom_idx]["ms"] for k in kern]))
+    dom_name = "group_kernel<%d, %d, %s>" % (dom["threads_per_instance"], dom["cols_per_thread"],
+                                             {0: "KM", 1: "BKM", 3: "AUCTION"}[dom["algo"]])
+
     # ---- e2e through the C-ABI with pinned host buffers ---------------------
     # one pinned slab per array kind, instances back to back
     ns = [C.shape[0] for C in Cs]
@@ -497,9 +590,8 @@ def main():
         peak, peak_kind = _peaks()
         # algorithmic bytes: cost elements the scans must read (2 bytes each
         # for rows packed to 16 bits) plus the batched-KM row reduction
-        alg_bytes = (st.get("read_bytes") or st["cost_bytes"]) + st["init_bytes"]
-        kern_ms = float(np.mean(step_ms))
-        achieved = alg_bytes / (kern_ms / 1000.0) / 1e9
+        alg_bytes = dom["read_bytes"] + dom["init_bytes"]
+        achieved = alg_bytes / (dom_ms / 1000.0) / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -510,9 +602,13 @@ def main():
                        "cost_bytes_resident": h2d_bytes, "l2": "inputs larger than L2 (%.0f MB > 129 MB)" % (h2d_bytes / 1e6),
                        "parallelism": f"replicas x{world} (instances sharded, no collective)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "ot::group_kernel (batched)", "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_launch": alg_bytes},
+                         "frac": achieved / peak, "traffic": measured_traffic(dom_name),
+                         "kernel": dom_name, "peak_kind": peak_kind, "launch_ms": dom_ms,
+                         "instances_per_launch": dom["instances"],
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "step_kernels": [{"kernel": "group_kernel<%d, %d, %s>" % (
+                             k["threads_per_instance"], k["cols_per_thread"], {0: "KM", 1: "BKM", 3: "AUCTION"}[k["algo"]]),
+                             "instances": k["instances"], "ms": k["ms"]} for k in kern[-1]]},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
                     "d2h_bytes_per_step": d2h_bytes},
             "gpu_launches": int(launches_per_step * args.steps),
@@ -567,6 +663,7 @@ def main():
         torch.cuda.empty_cache()
         line["single_4096"] = measure_single_4096(stream, ot, torch)
         line["single_16384"] = measure_single_16384(ctx, stream, ot, torch)
+        line["sinkhorn_4096"] = measure_sinkhorn_4096(stream, ot, torch)
         line["served"] = measure_served(ctx, stream, ot, torch, dev, args)
     elif rank == 0:
         line["cpu_baseline"] = None

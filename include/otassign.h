@@ -181,6 +181,25 @@ int ot_sinkhorn_solve(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int
  * launches that call made.  *total is a host pointer. */
 int ot_last_call_stats(ot_ctx* ctx, ot_stats* total);
 
+/* One kernel launch of the most recent ot_assign_solve / _stats / _batched
+ * call: the instances of one size bucket solved by one engine shape. */
+typedef struct ot_launch_info {
+  int32_t algo;                  /* OT_KM, OT_BKM or OT_AUCTION */
+  int32_t threads_per_instance;  /* group shape (auction: threads per CTA) */
+  int32_t cols_per_thread;       /* group shape (auction: 0) */
+  int32_t instances;
+  float ms;                      /* device time of the kernel (CUDA events around it), -1 if unknown */
+  int32_t reserved;
+  int64_t read_bytes;            /* cost bytes its scans loaded (as ot_stats.reserved[1]) */
+  int64_t init_bytes;            /* row-reduction / range-pass bytes */
+} ot_launch_info;
+
+/* Synchronises, then describes the group- and auction-engine launches of
+ * the most recent solve call (instances handed to the cluster engine are
+ * not listed): *count receives their number, out[0 .. min(count, max)-1]
+ * their descriptions. */
+int ot_last_call_launches(ot_ctx* ctx, ot_launch_info* out, int32_t max, int32_t* count);
+
 /* Solve k independent instances in one launch set (multi-instance
  * batching).  The array arguments are HOST arrays of length k; their
  * elements (C[t], row_to_col[t], u[t], v[t]) are device pointers, or all host

@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "otassign.h"
 #include "ot_ctx.h"
 #include "ot_group.cuh"
@@ -94,6 +96,61 @@ int ctx_fail(ot_ctx* ctx, int code, const std::string& msg) {
 int ctx_cuda(ot_ctx* ctx, cudaError_t e, const char* where) {
   if (e == cudaSuccess) return OT_OK;
   return ctx_fail(ctx, OT_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+namespace {
+
+using PtrAttrsFn = CUresult (*)(unsigned int, CUpointer_attribute*, void**, CUdeviceptr);
+
+// cuPointerGetAttributes through the runtime's driver entry point (no link
+// against the driver library); null if unavailable.
+PtrAttrsFn ptr_attrs_fn() {
+  static const PtrAttrsFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttributes", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<PtrAttrsFn>(f);
+  }();
+  return fn;
+}
+
+}  // namespace
+
+bool PtrKinds::on_device(const void* p) {
+  if (!p) return false;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  if (last_ < ranges_.size() && a >= ranges_[last_].lo && a < ranges_[last_].hi) return ranges_[last_].dev;
+  auto it = std::upper_bound(ranges_.begin(), ranges_.end(), a,
+                             [](uintptr_t x, const Range& r) { return x < r.lo; });
+  if (it != ranges_.begin()) {
+    const size_t i = size_t(it - ranges_.begin()) - 1;
+    if (a < ranges_[i].hi) {
+      last_ = i;
+      return ranges_[i].dev;
+    }
+  }
+  if (PtrAttrsFn fn = ptr_attrs_fn()) {
+    CUpointer_attribute at[4] = {CU_POINTER_ATTRIBUTE_MEMORY_TYPE, CU_POINTER_ATTRIBUTE_IS_MANAGED,
+                                 CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, CU_POINTER_ATTRIBUTE_RANGE_SIZE};
+    unsigned long long type = 0, managed = 0, start = 0, size = 0;
+    void* data[4] = {&type, &managed, &start, &size};
+    if (fn(4, at, data, CUdeviceptr(a)) == CUDA_SUCCESS && size > 0 && a >= start && a - start < size &&
+        (managed != 0 || type == CU_MEMORYTYPE_DEVICE || type == CU_MEMORYTYPE_HOST)) {
+      const bool dev = managed != 0 || type == CU_MEMORYTYPE_DEVICE;
+      const Range r{uintptr_t(start), uintptr_t(start + size), dev};
+      last_ = size_t(std::upper_bound(ranges_.begin(), ranges_.end(), r.lo,
+                                      [](uintptr_t x, const Range& y) { return x < y.lo; }) -
+                     ranges_.begin());
+      ranges_.insert(ranges_.begin() + last_, r);
+      return dev;
+    }
+  }
+  return ptr_on_device(p);  // memory the driver does not track (pageable host)
 }
 
 bool ptr_on_device(const void* p) {
@@ -243,7 +300,7 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
     return !(e && std::atoi(e) == 0);
   }();
   bool any_pack = false;
-  if (pack_on && !buckets.empty()) {
+  if (pack_on && slot.pack && !buckets.empty()) {
     size_t nrows = 0, nelem = 0;
     for (auto& kv : buckets)
       if (kv.second.algo != kAlgoAuction)
@@ -330,11 +387,41 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
     slot.meta_valid = true;
   }
 
+  // timing events around every bucket's kernel (external records, so that
+  // they become event-record nodes when the launch is captured in a graph)
+  if (slot.timing && slot.tev.size() < size_t(2 * nb)) {
+    slot.clear_graphs();
+    for (cudaEvent_t ev : slot.tev) cudaEventDestroy(ev);
+    slot.tev.assign(size_t(2 * nb), nullptr);
+    for (auto& ev : slot.tev)
+      if (cudaEventCreate(&ev) != cudaSuccess) {
+        slot.tev.clear();
+        slot.timing = false;
+        return ctx_fail(ctx, OT_ERR_CUDA, "timing events");
+      }
+  }
+  slot.last_buckets.clear();
+  for (auto& kv : buckets) {
+    const Bucket& b = kv.second;
+    LaunchSlot::BucketInfo bi;
+    bi.algo = b.algo;
+    bi.tpi = b.algo == kAlgoAuction ? b.shape : group_shape(b.shape).tpi;
+    bi.k = b.algo == kAlgoAuction ? 0 : group_shape(b.shape).k;
+    bi.idx = b.idx;
+    slot.last_buckets.push_back(std::move(bi));
+  }
+  const bool timed = slot.timing && !slot.tev.empty();
   auto launch_bucket = [&](const Bucket& b, int bi, cudaStream_t s) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    if (timed && (e = cudaEventRecordWithFlags(slot.tev[2 * bi], s, cudaEventRecordExternal)) != cudaSuccess)
+      return e;
     if (b.algo == kAlgoAuction)
-      return launch_auction(b.shape, dinst, dorder + offs[bi], int(b.idx.size()), dwork + bi, b.mmax, s);
-    return launch_group(group_shape(b.shape), b.algo, dinst, dorder + offs[bi], int(b.idx.size()), dwork + bi,
-                        b.nmax, b.mmax, max_ctas_env(), s);
+      e = launch_auction(b.shape, dinst, dorder + offs[bi], int(b.idx.size()), dwork + bi, b.mmax, s);
+    else
+      e = launch_group(group_shape(b.shape), b.algo, dinst, dorder + offs[bi], int(b.idx.size()), dwork + bi,
+                       b.nmax, b.mmax, max_ctas_env(), s);
+    if (e == cudaSuccess && timed) e = cudaEventRecordWithFlags(slot.tev[2 * bi + 1], s, cudaEventRecordExternal);
+    return e;
   };
   auto enqueue = [&](cudaStream_t s) -> cudaError_t {
     cudaError_t e = cudaMemsetAsync(dwork, 0, work_bytes, s);
@@ -396,7 +483,7 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
   cudaEventRecord(slot.meta_ev, stream);
   slot.meta_pending = true;
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "batch launch");
-  slot.last_launches = nb;
+  slot.last_launches = nb + (any_pack && nb > 0 ? 1 : 0);  // bucket kernels and the packing kernel
   return OT_OK;
 }
 
@@ -425,13 +512,14 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
   int first = -1;
   for (int t = 0; t < k; ++t)
     if (n[t] > 0) { first = t; break; }
-  const bool dev = first < 0 ? ptr_on_device(cost) : ptr_on_device(C[first]);
+  PtrKinds kinds;  // one driver query per allocation, not per pointer
+  const bool dev = first < 0 ? kinds.on_device(cost) : kinds.on_device(C[first]);
 
   std::vector<int> st(k, OT_OK), skip(k, 0);
   for (int t = 0; t < k; ++t) {
     st[t] = check_sizes(C[t], ldc[t], n[t], m[t]);
     if (st[t] == OT_OK && n[t] > 0 && !r2c[t]) st[t] = OT_ERR_ARG;
-    if (st[t] == OT_OK && n[t] > 0 && ptr_on_device(C[t]) != dev) st[t] = OT_ERR_ARG;
+    if (st[t] == OT_OK && n[t] > 0 && kinds.on_device(C[t]) != dev) st[t] = OT_ERR_ARG;
     skip[t] = st[t] != OT_OK;
   }
 
@@ -652,6 +740,8 @@ void LaunchSlot::release() {
   if (meta_pending && meta_ev) cudaEventSynchronize(meta_ev);
   meta_pending = false;
   clear_graphs();
+  for (cudaEvent_t ev : tev) cudaEventDestroy(ev);
+  tev.clear();
   d_meta.release();
   d_stats.release();
   d_pack.release();
@@ -689,6 +779,7 @@ int ot_ctx_create(ot_ctx** out, const ot_config* cfg) {
     if (cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess) { ot_ctx_destroy(ctx); return OT_ERR_CUDA; }
   if (ctx->api.init() != OT_OK) { ot_ctx_destroy(ctx); return OT_ERR_CUDA; }
   ctx->api.use_graphs = true;
+  ctx->api.timing = true;
   default_table(ctx->table);
   default_auto(ctx->auto_algo);
   if (c.tune_file) {
@@ -800,6 +891,47 @@ int ot_last_call_stats(ot_ctx* ctx, ot_stats* total) {
     }
   }
   total->reserved[0] = ctx->api.last_launches;
+  return OT_OK;
+}
+
+int ot_last_call_launches(ot_ctx* ctx, ot_launch_info* out, int32_t max, int32_t* count) {
+  if (!ctx || !count || max < 0 || (max > 0 && !out)) return OT_ERR_ARG;
+  std::lock_guard<std::mutex> lock(ctx->api_mu);
+  cudaSetDevice(ctx->device);
+  LaunchSlot& slot = ctx->api;
+  if (slot.meta_pending) cudaEventSynchronize(slot.meta_ev);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "sync");
+  const int nb = int(slot.last_buckets.size());
+  *count = nb;
+  std::vector<int64_t> h;
+  const int k = ctx->last_k;
+  if (k > 0 && slot.d_stats.ptr) {
+    h.resize(size_t(k) * 8);
+    if ((e = cudaMemcpy(h.data(), slot.d_stats.ptr, h.size() * sizeof(int64_t), cudaMemcpyDeviceToHost)) !=
+        cudaSuccess)
+      return ctx_cuda(ctx, e, "stats copy");
+  }
+  for (int b = 0; b < nb && b < max; ++b) {
+    const LaunchSlot::BucketInfo& bi = slot.last_buckets[b];
+    ot_launch_info& o = out[b];
+    std::memset(&o, 0, sizeof(o));
+    o.algo = bi.algo == kAlgoAuction ? OT_AUCTION : bi.algo;
+    o.threads_per_instance = bi.tpi;
+    o.cols_per_thread = bi.k;
+    o.instances = int32_t(bi.idx.size());
+    o.ms = -1.0f;
+    if (slot.timing && slot.tev.size() >= size_t(2 * nb)) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, slot.tev[2 * b], slot.tev[2 * b + 1]) == cudaSuccess) o.ms = ms;
+      else cudaGetLastError();
+    }
+    for (int t : bi.idx) {
+      if (size_t(t) * 8 + 7 >= h.size()) continue;
+      o.read_bytes += h[size_t(t) * 8 + 7];
+      o.init_bytes += h[size_t(t) * 8 + 5];
+    }
+  }
   return OT_OK;
 }
 

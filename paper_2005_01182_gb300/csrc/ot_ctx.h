@@ -62,6 +62,16 @@ struct LaunchSlot {
   bool meta_pending = false;
   std::vector<char> last_meta, pending;  // descriptor bytes on the device / being built
   bool meta_valid = false;               // last_meta matches d_meta
+  bool pack = true;                      // 16-bit row packing for group-engine buckets
+  // per-bucket kernel timing of the latest launch (API slot only): events
+  // recorded around each bucket's kernel (event-record nodes inside graphs)
+  bool timing = false;
+  std::vector<cudaEvent_t> tev;  // 2 per bucket
+  struct BucketInfo {
+    int algo, tpi, k;
+    std::vector<int> idx;
+  };
+  std::vector<BucketInfo> last_buckets;
   bool use_graphs = false;
   std::map<std::string, cudaGraphExec_t> graphs;
   int last_launches = 0;
@@ -116,6 +126,20 @@ struct StreamScope {
 int ctx_fail(ot_ctx* ctx, int code, const std::string& msg);
 int ctx_cuda(ot_ctx* ctx, cudaError_t e, const char* where);
 bool ptr_on_device(const void* p);
+// ptr_on_device for many pointers: the address range of every allocation
+// met is remembered, so pointers into one allocation cost one driver query.
+class PtrKinds {
+ public:
+  bool on_device(const void* p);
+
+ private:
+  struct Range {
+    uintptr_t lo, hi;
+    bool dev;
+  };
+  std::vector<Range> ranges_;  // sorted by lo, disjoint
+  size_t last_ = 0;
+};
 void load_tune_file(ot_ctx* ctx);
 // Bucket the instances by tuned group shape and launch them on `stream`
 // (forking buckets over the context's streams when `fork`).  Entries with

@@ -35,12 +35,25 @@ enum { kAlgoKM = 0, kAlgoBKM = 1, kAlgoAuction = 2 };  // auction: ot_auction.cu
 // status codes written by the device (match OT_ERR_* in otassign.h)
 enum { kDevOk = 0, kDevStepLimit = -4 };
 
-struct Best {
-  long long d;
+// (distance, column) pair of an argmin.  V = long long in general; int when
+// the instance's rows are packed to 16 bits, where every distance and dual of
+// the (row-shifted) problem stays below 2^31 (see solve_instance).
+template <typename V>
+struct BestT {
+  V d;
   int j;
 };
+using Best = BestT<long long>;
 
-__device__ __forceinline__ bool lex_less(long long d1, int j1, long long d2, int j2) {
+template <typename V>
+__device__ __forceinline__ constexpr V inf_of();
+template <>
+__device__ __forceinline__ constexpr long long inf_of<long long>() { return kInf; }
+template <>
+__device__ __forceinline__ constexpr int inf_of<int>() { return INT_MAX; }
+
+template <typename V>
+__device__ __forceinline__ bool lex_less(V d1, int j1, V d2, int j2) {
   return d1 < d2 || (d1 == d2 && j1 < j2);
 }
 
@@ -57,6 +70,14 @@ __device__ __forceinline__ Best warp_argmin(Best b) {
   const unsigned mj = __reduce_min_sync(0xffffffffu, (hi == mh && lo == ml) ? unsigned(b.j) : 0xffffffffu);
   const unsigned long long mk = (static_cast<unsigned long long>(mh) << 32) | ml;
   return Best{static_cast<long long>(mk ^ 0x8000000000000000ull), int(mj)};
+}
+
+// The same for 32-bit distances: two warp reductions.
+__device__ __forceinline__ BestT<int> warp_argmin(BestT<int> b) {
+  const unsigned key = static_cast<unsigned>(b.d) ^ 0x80000000u;
+  const unsigned mk = __reduce_min_sync(0xffffffffu, key);
+  const unsigned mj = __reduce_min_sync(0xffffffffu, key == mk ? unsigned(b.j) : 0xffffffffu);
+  return BestT<int>{static_cast<int>(mk ^ 0x80000000u), int(mj)};
 }
 
 __device__ __forceinline__ long long warp_sum(long long x) {
@@ -121,8 +142,9 @@ __device__ inline GroupSmem carve(unsigned char* p, int tpi, int algo, int nmax,
 }
 
 // Minimum (dist, column) over the group; every thread gets the result.
-template <int TPI>
-__device__ __forceinline__ Best group_argmin(Best b, Best* slots, int& parity) {
+// The slots hold 2 x TPI/32 pairs of either width.
+template <int TPI, typename V>
+__device__ __forceinline__ BestT<V> group_argmin(BestT<V> b, Best* slots, int& parity) {
   b = warp_argmin(b);
   if constexpr (TPI == 32) {
     __syncwarp();
@@ -130,11 +152,11 @@ __device__ __forceinline__ Best group_argmin(Best b, Best* slots, int& parity) {
   } else {
     constexpr int NW = TPI / 32;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    Best* s = slots + parity * NW;
+    BestT<V>* s = reinterpret_cast<BestT<V>*>(slots) + parity * NW;
     parity ^= 1;
     if (l == 0) s[w] = b;
     __syncthreads();
-    Best c = (l < NW) ? s[l] : Best{kInf, INT_MAX};
+    BestT<V> c = (l < NW) ? s[l] : BestT<V>{inf_of<V>(), INT_MAX};
     return warp_argmin(c);
   }
 }
@@ -156,22 +178,23 @@ __device__ __forceinline__ long long group_sum(long long x, Best* slots, int& pa
   }
 }
 
-// Solve one instance with the whole group.  t = thread index in the group.
-template <int TPI, int K, int ALGO>
-__device__ void solve_instance(const Instance& I, const GroupSmem& S, const int t) {
+// Solve one instance with the whole group.  t = thread index in the group;
+// V is the type of distances and duals in registers (see solve_instance).
+template <int TPI, int K, int ALGO, typename V>
+__device__ __forceinline__ void solve_instance_v(const Instance& I, const GroupSmem& S, const int t,
+                                                 const bool pk) {
   const int n = I.n, m = I.m;
   const int32_t* __restrict__ C = I.C;
   const long long ldc = I.ldc;
-  // 16-bit packed rows (row-shifted costs) when the packing pass succeeded
-  const bool pk = I.P != nullptr && *I.pok != 0;
   const uint16_t* __restrict__ P = I.P;
   int rpar = 0;  // reduction-slot parity
+  constexpr V kInfV = inf_of<V>();
 
-  long long dist[K], v[K];
+  V dist[K], v[K];
   int pred[K];
   unsigned inT = 0;
 #pragma unroll
-  for (int k = 0; k < K; ++k) { v[k] = 0; dist[k] = kInf; pred[k] = -1; }
+  for (int k = 0; k < K; ++k) { v[k] = 0; dist[k] = kInfV; pred[k] = -1; }
 
   for (int i = t; i < n; i += TPI) { S.r2c[i] = -1; S.u[i] = 0; }
   for (int j = t; j < m; j += TPI) { S.c2r[j] = -1; S.pred[j] = -1; }
@@ -209,11 +232,11 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
   while (matched < n) {
     ++phases;
 #pragma unroll
-    for (int k = 0; k < K; ++k) { dist[k] = kInf; pred[k] = -1; }
+    for (int k = 0; k < K; ++k) { dist[k] = kInfV; pred[k] = -1; }
     inT = 0;
     int L = 1;
     int km_row = matched;  // KM roots rows in index order
-    long long level = 0;
+    V level = 0;
     int tcount = 0;
 
     if constexpr (ALGO == kAlgoBKM) {
@@ -239,14 +262,14 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
       // A1 / B2: scan the rows that just joined the tree, columns outside T
       if constexpr (ALGO == kAlgoKM) {
         const int i = km_row;
-        const long long base = level - S.u[i];
+        const V base = level - V(S.u[i]);
         const int32_t* row = C + i * ldc;
         const uint16_t* prow = P + (long long)i * m;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           const int j = t + k * TPI;
           if (j < m && !((inT >> k) & 1u)) {
-            const long long cand = base + (pk ? int(__ldg(prow + j)) : __ldg(row + j)) - v[k];
+            const V cand = base + V(pk ? int(__ldg(prow + j)) : __ldg(row + j)) - v[k];
             if (cand < dist[k]) {
               dist[k] = cand;
               pred[k] = i;
@@ -276,12 +299,12 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
             const int q = q0 + e;
             if (q >= L) break;
             const int i = S.list[q];
-            const long long base = level - S.u[i];
+            const V base = level - V(S.u[i]);
 #pragma unroll
             for (int k = 0; k < K; ++k) {
               const int j = t + k * TPI;
               if (j < m && !((inT >> k) & 1u)) {
-                const long long cand = base + cc[e][k] - v[k];
+                const V cand = base + V(cc[e][k]) - v[k];
                 if (cand < dist[k] || (cand == dist[k] && i < pred[k])) { dist[k] = cand; pred[k] = i; }
               }
             }
@@ -294,14 +317,14 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
       read_bytes += (pk ? 2LL : 4LL) * L * (m - tcount);
 
       // A2 / B4: minimum distance outside T, lowest column on ties
-      Best b{kInf, INT_MAX};
+      BestT<V> b{kInfV, INT_MAX};
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int j = t + k * TPI;
-        if (j < m && !((inT >> k) & 1u) && lex_less(dist[k], j, b.d, b.j)) b = Best{dist[k], j};
+        if (j < m && !((inT >> k) & 1u) && lex_less(dist[k], j, b.d, b.j)) b = BestT<V>{dist[k], j};
       }
-      b = group_argmin<TPI>(b, S.slots, rpar);
-      const long long D = b.d;
+      b = group_argmin<TPI, V>(b, S.slots, rpar);
+      const V D = b.d;
       if (b.j == INT_MAX) { status = kDevStepLimit; break; }
 
       if constexpr (ALGO == kAlgoKM) {
@@ -326,7 +349,7 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           if ((inT >> k) & 1u) {
-            const long long dd = D - dist[k];
+            const V dd = D - dist[k];
             v[k] -= dd;
             S.u[S.c2r[t + k * TPI]] += dd;
           }
@@ -382,7 +405,7 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           if ((inT >> k) & 1u) {
-            const long long dd = D - dist[k];
+            const V dd = D - dist[k];
             v[k] -= dd;
             S.u[S.c2r[t + k * TPI]] += dd;
           }
@@ -466,6 +489,23 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
   group_sync<TPI>();
   if (t == 0 && I.status) *reinterpret_cast<volatile int32_t*>(I.status) = status;
   group_sync<TPI>();
+}
+
+// Packed instances run on 32-bit distances and duals.  After the row shift
+// every cost lies in [0, 65535] = [0, R].  Each dual adjustment raises the
+// dual objective sum(u) + sum(v) by at least the step's delta (KM: the root
+// gains D and the other changes cancel pairwise; batched KM: at least one free
+// root gains D), the objective never exceeds OPT <= n R and starts at 0, so
+// every dual moves by at most n R in total and every distance of a phase is
+// at most n R.  A candidate level - u_i + c_ij - v_j is then below
+// 3 n R + R < 2^31 for n <= 8191 (the group engine has n <= m <= 4096).
+template <int TPI, int K, int ALGO>
+__device__ void solve_instance(const Instance& I, const GroupSmem& S, const int t) {
+  const bool pk = I.P != nullptr && *I.pok != 0;
+  if (pk && I.n <= 8191)
+    solve_instance_v<TPI, K, ALGO, int>(I, S, t, true);
+  else
+    solve_instance_v<TPI, K, ALGO, long long>(I, S, t, pk);
 }
 
 template <int TPI, int K, int ALGO>

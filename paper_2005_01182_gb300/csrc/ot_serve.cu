@@ -153,6 +153,9 @@ int ServeState::start() {
     cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking);
     cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming);
     if (w.slot.init() != OT_OK) return OT_ERR_CUDA;
+    // serving waves mix sizes up to m = 4096 and solve each wave once: the
+    // extra pass of 16-bit packing costs more than it saves (measured)
+    w.slot.pack = false;
   }
   if (cudaGetLastError() != cudaSuccess) return OT_ERR_CUDA;
   started = true;
@@ -239,7 +242,9 @@ void ServeState::loop() {
   while (!stop) {
     cv.wait_for(lk, std::chrono::microseconds(200));
     if (stop) break;
-    // admit queued requests, oldest first, while space allows
+    // admit queued requests, oldest first, while space allows; their copies
+    // go out back to back and are waited for once
+    std::vector<uint64_t> admitted;
     while (!pending.empty()) {
       const uint64_t t = pending.front();
       auto it = reqs.find(t);
@@ -249,9 +254,14 @@ void ServeState::loop() {
       pending.pop_front();
       cudaMemcpyAsync(arena.base + r.off, r.host_C.data(), 4 * size_t(r.n) * r.m,
                       cudaMemcpyHostToDevice, copy_stream);
+      admitted.push_back(t);
+    }
+    if (!admitted.empty()) {
       cudaStreamSynchronize(copy_stream);
-      std::vector<int32_t>().swap(r.host_C);
-      ready.push_back(t);
+      for (uint64_t t : admitted) {
+        std::vector<int32_t>().swap(reqs[t].host_C);
+        ready.push_back(t);
+      }
     }
     launch_ready();
   }

@@ -101,6 +101,7 @@ def load(path: str | None = None):
         "ot_sinkhorn_solve": (ctypes.c_int, [vp, vp, i64, i32, i32, vp, vp, ctypes.c_double, ctypes.c_double,
                                              i32, vp, vp, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), vp]),
+        "ot_last_call_launches": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32)]),
         "ot_version": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -283,6 +284,22 @@ def ot_transport_solve(ctx: Context, C: torch.Tensor, supply, demand, algo: int 
                                     _stream_handle(stream))
     ctx._raise(rc, "ot_transport_solve")
     return flow, int(c.item())
+
+
+class ot_launch_info(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int32), ("threads_per_instance", ctypes.c_int32),
+                ("cols_per_thread", ctypes.c_int32), ("instances", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("reserved", ctypes.c_int32), ("read_bytes", ctypes.c_int64), ("init_bytes", ctypes.c_int64)]
+
+
+def ot_last_call_launches(ctx: Context) -> list:
+    """Per-launch description of the most recent solve call (synchronises):
+    algorithm, shape, instances, device ms and bytes of each bucket kernel."""
+    buf = (ot_launch_info * 64)()
+    cnt = ctypes.c_int32()
+    ctx._raise(ctx.lib.ot_last_call_launches(ctx.h, buf, 64, ctypes.byref(cnt)), "ot_last_call_launches")
+    return [{f: getattr(buf[i], f) for f, _ in ot_launch_info._fields_ if f != "reserved"}
+            for i in range(min(cnt.value, 64))]
 
 
 def ot_sinkhorn_solve(ctx: Context, C: torch.Tensor, eta: float, eps_rel: float = 1e-3, max_iter: int = 1000,
