@@ -444,10 +444,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--skip-extras", action="store_true")
     ap.add_argument("--served-requests", type=int, default=1500)
-    ap.add_argument("--profile-once", default=None, choices=["batch", "n16384", "n8192"],
+    ap.add_argument("--profile-once", default=None,
+                    choices=["batch", "n16384", "n8192", "sinkhorn16384", "sinkhorn8192"],
                     help="untimed single run for an ncu capture: 'batch' = autotune, then 3 batched "
                          "OT_AUTO calls on the 4096-instance batch inside an NVTX range 'timed'; "
-                         "'n16384' / 'n8192' = one batched-KM solve on a grid instance")
+                         "'n16384' / 'n8192' = one batched-KM solve on a grid instance; "
+                         "'sinkhorn16384' / 'sinkhorn8192' = log-domain Sinkhorn, eta = 2, 3 / 2 "
+                         "fixed iterations on a 1024 x 1024-grid instance")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -474,6 +477,17 @@ def main():
     ctx = ot.Context(device=local)
     stream = torch.cuda.current_stream()
 
+    if args.profile_once in ("sinkhorn16384", "sinkhorn8192"):
+        big = args.profile_once == "sinkhorn16384"
+        C = W.single_16384() if big else W.grid_sqdist(8192, grid=1024)
+        Cd = torch.from_numpy(C).to(dev)
+        del C
+        f, g, (cost, res, it) = ot.ot_sinkhorn_solve(ctx, Cd, 2.0, eps_rel=0.0, max_iter=3 if big else 2,
+                                                     stream=stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_once": args.profile_once, "cost": cost, "iterations": it}))
+        ctx.close()
+        return
     if args.profile_once in ("n16384", "n8192"):
         n = 16384 if args.profile_once == "n16384" else 8192
         C = W.grid_sqdist(n, n, grid=1024 if n == 16384 else 724)

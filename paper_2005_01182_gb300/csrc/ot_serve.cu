@@ -11,6 +11,10 @@
 // reads without waiting for the rest of the wave.  poll() copies the
 // results out and frees the arena block, which lets queued requests in.
 #include <algorithm>
+
+#ifndef OT_SERVE_PACK
+#define OT_SERVE_PACK 1
+#endif
 #include <chrono>
 #include <cstring>
 
@@ -153,9 +157,9 @@ int ServeState::start() {
     cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking);
     cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming);
     if (w.slot.init() != OT_OK) return OT_ERR_CUDA;
-    // serving waves mix sizes up to m = 4096 and solve each wave once: the
-    // extra pass of 16-bit packing costs more than it saves (measured)
-    w.slot.pack = false;
+    // 16-bit packing of serving waves (an extra pass over each wave's
+    // matrices, and the 32-bit solver path for packed instances)
+    w.slot.pack = OT_SERVE_PACK != 0;
   }
   if (cudaGetLastError() != cudaSuccess) return OT_ERR_CUDA;
   started = true;
