@@ -647,13 +647,61 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
       if (e != cudaSuccess) return ctx_cuda(ctx, e, "H2D");
     }
   }
-  if (c_flat && first_live >= 0 && ec > 0) {
-    e = cudaMemcpyAsync(dC + off_c[first_live], C[first_live], 4 * (ec - off_c[first_live]),
-                        cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return ctx_cuda(ctx, e, "H2D");
-  }
+  // a large batch laid out back to back moves in chunks: chunk c is solved
+  // while chunks c+1.. are still being copied
+  int live = 0;
+  for (int t = 0; t < k; ++t) live += !skip[t];
+  const int nchunks = (c_flat && live >= 64 * kHostChunks && 4 * ec >= (size_t(64) << 20)) ? kHostChunks : 1;
   std::vector<int> unsup;
-  if (int rc = run_device_batch(ctx, ctx->api, insts, skip, algo, stream, true, true, &unsup, route_wide); rc) return rc;
+  if (nchunks > 1) {
+    if (int rc = ctx->api.d_stats.reserve(size_t(k) * 8 * sizeof(int64_t)); rc) return ctx_fail(ctx, rc, "stats alloc");
+    int64_t* dstats = static_cast<int64_t*>(ctx->api.d_stats.ptr);
+    for (int t = 0; t < k; ++t) insts[t].stats = dstats + size_t(t) * 8;
+    // chunk boundaries over the instances, balanced by matrix bytes
+    std::vector<int> bound(nchunks + 1, k);
+    bound[0] = 0;
+    for (int c = 1, t = 0; c < nchunks; ++c) {
+      const size_t want = (ec / nchunks) * c;
+      while (t < k && off_c[t] < want) ++t;
+      bound[c] = t;
+    }
+    if ((e = cudaEventRecord(ctx->hev_start, stream)) != cudaSuccess) return ctx_cuda(ctx, e, "chunk start");
+    for (int c = 0; c < nchunks; ++c) {
+      const size_t e0 = bound[c] < k ? off_c[bound[c]] : ec, e1 = bound[c + 1] < k ? off_c[bound[c + 1]] : ec;
+      if (e1 > e0) {
+        // the caller's buffer is contiguous from first_live on (c_flat)
+        const int32_t* src = C[first_live] + (e0 - off_c[first_live]);
+        if (e0 >= off_c[first_live] &&
+            (e = cudaMemcpyAsync(dC + e0, src, 4 * (e1 - e0), cudaMemcpyHostToDevice, ctx->copy_stream)) != cudaSuccess)
+          return ctx_cuda(ctx, e, "H2D chunk");
+      }
+      if ((e = cudaEventRecord(ctx->hev_copy[c], ctx->copy_stream)) != cudaSuccess) return ctx_cuda(ctx, e, "chunk copy");
+    }
+    int launches = 0;
+    for (int c = 0; c < nchunks; ++c) {
+      cudaStream_t cs = ctx->cstreams[c];
+      cudaStreamWaitEvent(cs, ctx->hev_start, 0);
+      cudaStreamWaitEvent(cs, ctx->hev_copy[c], 0);
+      std::vector<Instance> ci(insts.begin() + bound[c], insts.begin() + bound[c + 1]);
+      std::vector<int> cskip(skip.begin() + bound[c], skip.begin() + bound[c + 1]), cun;
+      if (int rc = run_device_batch(ctx, ctx->hslots[c], ci, cskip, algo, cs, false, false, &cun, route_wide); rc)
+        return rc;
+      for (int x : cun) unsup.push_back(bound[c] + x);
+      launches += ctx->hslots[c].last_launches;
+      cudaEventRecord(ctx->hev_done[c], cs);
+      cudaStreamWaitEvent(stream, ctx->hev_done[c], 0);
+    }
+    ctx->api.last_launches = launches;
+    ctx->api.last_buckets.clear();
+  } else {
+    if (c_flat && first_live >= 0 && ec > 0) {
+      e = cudaMemcpyAsync(dC + off_c[first_live], C[first_live], 4 * (ec - off_c[first_live]),
+                          cudaMemcpyHostToDevice, stream);
+      if (e != cudaSuccess) return ctx_cuda(ctx, e, "H2D");
+    }
+    if (int rc = run_device_batch(ctx, ctx->api, insts, skip, algo, stream, true, true, &unsup, route_wide); rc)
+      return rc;
+  }
   ctx->last_k = k;
   ctx->last_skip = skip;
   std::vector<int> still;
@@ -778,6 +826,21 @@ int ot_ctx_create(ot_ctx** out, const ot_config* cfg) {
   for (cudaEvent_t* ev : {&ctx->join_in_ev, &ctx->join_out_ev, &ctx->sjoin_in_ev, &ctx->sjoin_out_ev})
     if (cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess) { ot_ctx_destroy(ctx); return OT_ERR_CUDA; }
   if (ctx->api.init() != OT_OK) { ot_ctx_destroy(ctx); return OT_ERR_CUDA; }
+  if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->hev_start, cudaEventDisableTiming) != cudaSuccess) {
+    ot_ctx_destroy(ctx);
+    return OT_ERR_CUDA;
+  }
+  for (int c = 0; c < kHostChunks; ++c) {
+    if (cudaStreamCreateWithFlags(&ctx->cstreams[c], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->hev_copy[c], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->hev_done[c], cudaEventDisableTiming) != cudaSuccess ||
+        ctx->hslots[c].init() != OT_OK) {
+      ot_ctx_destroy(ctx);
+      return OT_ERR_CUDA;
+    }
+    ctx->hslots[c].use_graphs = true;
+  }
   ctx->api.use_graphs = true;
   ctx->api.timing = true;
   default_table(ctx->table);
@@ -798,6 +861,14 @@ void ot_ctx_destroy(ot_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   ctx->api.release();
+  for (int c = 0; c < kHostChunks; ++c) {
+    if (ctx->cstreams[c]) { cudaStreamSynchronize(ctx->cstreams[c]); cudaStreamDestroy(ctx->cstreams[c]); }
+    ctx->hslots[c].release();
+    if (ctx->hev_copy[c]) cudaEventDestroy(ctx->hev_copy[c]);
+    if (ctx->hev_done[c]) cudaEventDestroy(ctx->hev_done[c]);
+  }
+  if (ctx->copy_stream) { cudaStreamSynchronize(ctx->copy_stream); cudaStreamDestroy(ctx->copy_stream); }
+  if (ctx->hev_start) cudaEventDestroy(ctx->hev_start);
   for (int i = 0; i < kForkStreams; ++i) {
     if (ctx->bstreams[i]) { cudaStreamSynchronize(ctx->bstreams[i]); cudaStreamDestroy(ctx->bstreams[i]); }
     if (ctx->join_ev[i]) cudaEventDestroy(ctx->join_ev[i]);

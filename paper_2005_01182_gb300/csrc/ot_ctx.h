@@ -20,6 +20,9 @@ namespace ot {
 constexpr int kNumBuckets = 8;        // bucket b: m <= 32 << b
 constexpr int kMaxGroupCols = 4096;   // widest instance one group engine handles
 constexpr int kForkStreams = 4;
+// Host-pointer batches: matrices are copied in up to kHostChunks contiguous
+// chunks, each solved as soon as its copy has landed.
+constexpr int kHostChunks = 4;
 constexpr int kLargeEngine = -2;  // table entry: use the cluster engine
 // A batched-KM instance wider than kClusterRouteCols solved on its own
 // (ot_assign_solve / _stats) goes to the cluster engine instead of one group
@@ -93,6 +96,12 @@ struct ot_ctx {
   std::mutex api_mu;
 
   LaunchSlot api;
+  // pipelined host-pointer batches: a copy stream, one stream, launch slot
+  // and event set per chunk
+  cudaStream_t copy_stream = nullptr;
+  cudaStream_t cstreams[ot::kHostChunks] = {};
+  LaunchSlot hslots[ot::kHostChunks];
+  cudaEvent_t hev_start = nullptr, hev_copy[ot::kHostChunks] = {}, hev_done[ot::kHostChunks] = {};
   DevBuf d_status, d_io, d_scratch, d_large, d_scaled;
   std::mutex scaled_mu;
 
