@@ -508,8 +508,23 @@ __device__ void solve_instance(const Instance& I, const GroupSmem& S, const int 
     solve_instance_v<TPI, K, ALGO, long long>(I, S, t, pk);
 }
 
+// Resident warps per SM the group kernels may be compiled for (a register
+// cap through __launch_bounds__); 0 leaves the register count to the
+// compiler's heuristic for the block size alone.
+#ifndef OT_GROUP_MIN_WARPS
+#define OT_GROUP_MIN_WARPS 0
+#endif
+#if OT_GROUP_MIN_WARPS > 0
+#define OT_GROUP_BOUNDS(TPI_)                                                                     \
+  __launch_bounds__((TPI_) == 32 ? 256 : (TPI_), OT_GROUP_MIN_WARPS * 32 / ((TPI_) == 32 ? 256 : (TPI_)) > 1 \
+                                                      ? OT_GROUP_MIN_WARPS * 32 / ((TPI_) == 32 ? 256 : (TPI_)) \
+                                                      : 1)
+#else
+#define OT_GROUP_BOUNDS(TPI_) __launch_bounds__((TPI_) == 32 ? 256 : (TPI_))
+#endif
+
 template <int TPI, int K, int ALGO>
-__global__ void __launch_bounds__(TPI == 32 ? 256 : TPI)
+__global__ void OT_GROUP_BOUNDS(TPI)
     group_kernel(const Instance* __restrict__ insts, const int32_t* __restrict__ order, int num,
                  int* work, int nmax, int mmax, int groups_per_cta, int bytes_per_group) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
