@@ -106,6 +106,39 @@ def test_extreme_values(oracle_mod, ctx):
         check_bkm(oracle_mod, ctx, C, cost)
 
 
+def test_packed_32bit_path_limits(oracle_mod, ctx):
+    """Rows packed to 16 bits run on 32-bit distances and duals.  At the
+    bound of that path -- every row spans exactly 65535 above an offset near
+    the int32 extremes, n = m = 4096 -- KM must still equal the oracle bit
+    for bit, and a batch mixing packable rows with one row of range 65536
+    (64-bit path) must agree instance by instance."""
+    r = np.random.default_rng(23)
+    n = 4096
+    base = r.integers(-(1 << 31) + 70000, (1 << 31) - 70000, size=(n, 1))
+    C = (base + r.integers(0, 65536, size=(n, n))).astype(np.int64)
+    C[:, 0] = base[:, 0]
+    C[:, 1] = base[:, 0] + 65535
+    C = C.astype(np.int32)
+    cost = check_km(oracle_mod, ctx, C)
+    check_bkm(oracle_mod, ctx, C, cost)
+    mats = []
+    for t in range(6):
+        M = r.integers(0, 65536, size=(200 + t, 220)).astype(np.int32)
+        if t == 3:
+            M[7, 5] = 65536  # this instance cannot be packed
+            M[7, 6] = 0
+        mats.append(M)
+    b = ot.ot_assign_solve_batched(ctx, [torch.from_numpy(M).cuda() for M in mats], ot.OT_KM)
+    torch.cuda.synchronize()
+    for t, M in enumerate(mats):
+        a0, c0, u0, v0 = oracle_mod.km(M)
+        r_, u_, v_ = (x.cpu().numpy() for x in b.outs[t])
+        assert int(b.cost[t]) == c0
+        np.testing.assert_array_equal(r_, a0)
+        np.testing.assert_array_equal(u_, u0)
+        np.testing.assert_array_equal(v_, v0)
+
+
 def test_degenerate(oracle_mod, ctx):
     for n, m in [(0, 0), (0, 7)]:
         C = torch.zeros((n, m), dtype=torch.int32, device="cuda")
