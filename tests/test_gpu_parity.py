@@ -249,6 +249,27 @@ def test_single_4096(oracle_mod, ctx):
     check_bkm(oracle_mod, ctx, C, c)
 
 
+def test_default_stream_ordering(oracle_mod, ctx):
+    """NULL stream = the caller's default stream: a solve issued right after
+    torch writes the matrix on that stream sees the written values, and
+    torch's reads of the results after the call see the solve's output,
+    with no explicit synchronisation in between."""
+    C = W.uniform_costs(700, hi=50000, seed=31)
+    a0, c0, _, _ = oracle_mod.km(C)
+    src = torch.from_numpy(C).cuda()
+    for _ in range(3):
+        dst = torch.zeros_like(src)
+        big = torch.randn(4096, 4096, device="cuda")
+        for _ in range(4):
+            big = big @ big  # keeps the default stream busy before the copy
+        dst.copy_(src)
+        r, c, u, v = ot.ot_assign_solve(ctx, dst, ot.OT_KM, stream=0)
+        got_c = int(c.cpu().item())
+        assert got_c == c0
+        np.testing.assert_array_equal(r.cpu().numpy(), a0)
+        del big
+
+
 def test_host_pointers(oracle_mod, ctx):
     """The C-ABI with host buffers (pinned and pageable) stages through the
     device and returns the same result as the device path."""
