@@ -8,6 +8,8 @@
 
 namespace ot {
 
+constexpr int kPackRegs = 8;  // rows up to 256 columns are packed from registers
+
 __global__ void __launch_bounds__(256) pack_kernel(const Instance* __restrict__ insts,
                                                    const int32_t* __restrict__ order, int num) {
   const Instance I = insts[order ? order[blockIdx.x] : blockIdx.x];
@@ -19,6 +21,41 @@ __global__ void __launch_bounds__(256) pack_kernel(const Instance* __restrict__ 
   const int n = I.n, m = I.m;
   uint16_t* P = const_cast<uint16_t*>(I.P);
   int32_t* roff = const_cast<int32_t*>(I.roff);
+  if (m <= 32 * kPackRegs) {
+    // the row stays in registers: all its loads in flight at once, one read
+    for (int i = warp; i < n; i += nwarps) {
+      const int32_t* row = I.C + (long long)i * I.ldc;
+      int c[kPackRegs];
+#pragma unroll
+      for (int q = 0; q < kPackRegs; ++q) {
+        const int j = lane + 32 * q;
+        c[q] = j < m ? __ldg(row + j) : 0;
+      }
+      int mn = INT_MAX, mx = INT_MIN;
+#pragma unroll
+      for (int q = 0; q < kPackRegs; ++q)
+        if (lane + 32 * q < m) {
+          mn = min(mn, c[q]);
+          mx = max(mx, c[q]);
+        }
+      mn = __reduce_min_sync(0xffffffffu, mn);
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      if ((long long)mx - (long long)mn > 65535) {
+        if (lane == 0) ok = 0;
+        continue;
+      }
+      uint16_t* prow = P + (long long)i * m;
+#pragma unroll
+      for (int q = 0; q < kPackRegs; ++q) {
+        const int j = lane + 32 * q;
+        if (j < m) prow[j] = static_cast<uint16_t>(c[q] - mn);
+      }
+      if (lane == 0) roff[i] = mn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *const_cast<int32_t*>(I.pok) = ok;
+    return;
+  }
   for (int i = warp; i < n; i += nwarps) {
     const int32_t* row = I.C + (long long)i * I.ldc;
     int mn = INT_MAX, mx = INT_MIN;
