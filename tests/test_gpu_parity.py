@@ -291,16 +291,22 @@ def test_host_pointers(oracle_mod, ctx):
         assert oracle_mod.check_certificate(C, r, u, v, int(a.cost[t])) == 0
 
 
-def test_host_slab_batch_pipelined(oracle_mod, ctx):
-    """A large batch in one pinned host slab (>= 256 instances, >= 64 MB)
-    is copied and solved chunk by chunk; results equal the device path bit
-    for bit (KM), including a skipped empty instance and a ragged tail."""
+@pytest.mark.parametrize("mode", ["pinned", "pageable"])
+def test_host_slab_batch_pipelined(oracle_mod, ctx, mode):
+    """A large batch in one host slab (>= 256 instances, >= 64 MB) is copied
+    and solved chunk by chunk; results equal the device path bit for bit
+    (KM), including a skipped empty instance, an instance whose rows span
+    more than 16 bits and a ragged tail."""
     rng = np.random.default_rng(17)
     sizes = [int(x) for x in rng.integers(240, 301, size=300)] + [0, 37]
-    mats = [W.uniform_costs(n, hi=60000, seed=i) if n else np.zeros((0, 5), np.int32) for i, n in enumerate(sizes)]
+    # instance 5 spans more than 16 bits (not packed: solved from the staged copy)
+    mats = [W.uniform_costs(n, hi=(1 << 20) if i == 5 else 60000, seed=i) if n else np.zeros((0, 5), np.int32)
+            for i, n in enumerate(sizes)]
     total = sum(C.size for C in mats)
     assert 4 * total >= 64 << 20
-    slab = torch.empty(total, dtype=torch.int32).pin_memory()
+    slab = torch.empty(total, dtype=torch.int32)
+    if mode != "pageable":
+        slab = slab.pin_memory()
     hC, o = [], 0
     for C in mats:
         v = slab[o:o + C.size].view(C.shape)
@@ -317,7 +323,7 @@ def test_host_slab_batch_pipelined(oracle_mod, ctx):
             continue
         np.testing.assert_array_equal(ah.outs[t][0].numpy(), ad.outs[t][0].cpu().numpy())
         np.testing.assert_array_equal(ah.outs[t][2].numpy(), ad.outs[t][2].cpu().numpy())
-    for t in (0, 150, 301):
+    for t in (0, 5, 150, 301):
         assert int(ah.cost[t]) == oracle_mod.km(mats[t])[1]
     st = ot.ot_last_call_stats(ctx)
     assert st["launches"] >= 1
