@@ -75,12 +75,13 @@ struct AuctionSmem {
   int* list;          // [N] bidders of the round
   long long* red;     // [64] block reductions
   int* misc;          // [8]
+  Bid* part;          // [32] per-warp partial bids (a bidder split over warps)
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
 __host__ __device__ inline size_t auction_bytes(int N) {
-  return 3 * al16(8 * size_t(N)) + 5 * al16(4 * size_t(N)) + 8 * 64 + 4 * 8;
+  return 3 * al16(8 * size_t(N)) + 5 * al16(4 * size_t(N)) + 8 * 64 + 4 * 8 + 32 * sizeof(Bid);
 }
 
 __device__ AuctionSmem carve_auction(unsigned char* base, int N) {
@@ -95,7 +96,8 @@ __device__ AuctionSmem carve_auction(unsigned char* base, int N) {
   S.held = reinterpret_cast<int*>(base + o); o += al16(4 * size_t(N));
   S.obj = reinterpret_cast<int*>(base + o); o += al16(4 * size_t(N));
   S.list = reinterpret_cast<int*>(base + o); o += al16(4 * size_t(N));
-  S.misc = reinterpret_cast<int*>(base + o);
+  S.misc = reinterpret_cast<int*>(base + o); o += 4 * 8;
+  S.part = reinterpret_cast<Bid*>(base + o);
   return S;
 }
 
@@ -188,13 +190,14 @@ __device__ __forceinline__ void auction_instance(const Instance& I, const Auctio
       }
       ++rounds;
       bids += U;
-      // bids against the round-start prices, one warp per bidder
-      for (int x = wid; x < U; x += W) {
-        const int i = S.list[x];
+      // bids against the round-start prices: the lanes of a warp stride the
+      // bidder's row (several loads in flight), then a butterfly merge
+      auto scan = [&](int i, int j0, int jstep) {
         Bid b{kWInf, INT_MAX, kWInf};
         if (i < n) {
           const int32_t* row = I.C + i * ldc;
-          for (int j = lane; j < N; j += 32) {
+#pragma unroll 4
+          for (int j = j0; j < N; j += jstep) {
             const long long w = ((long long)__ldg(row + j) - cmin) * scale + S.p[j];
             if (w < b.w1) {
               b.w2 = b.w1;
@@ -205,7 +208,8 @@ __device__ __forceinline__ void auction_instance(const Instance& I, const Auctio
             }
           }
         } else {
-          for (int j = lane; j < N; j += 32) {
+#pragma unroll 4
+          for (int j = j0; j < N; j += jstep) {
             const long long w = S.p[j];
             if (w < b.w1) {
               b.w2 = b.w1;
@@ -216,15 +220,40 @@ __device__ __forceinline__ void auction_instance(const Instance& I, const Auctio
             }
           }
         }
-        b = warp_merge(b);
-        if (lane == 0) {
-          const long long w2 = N == 1 ? b.w1 : b.w2;
-          const long long a = S.p[b.j1] + (w2 - b.w1) + eps;
-          S.obj[i] = b.j1;
-          S.amt[i] = a;
-          atomicMax(&S.best[b.j1], a);
+        return warp_merge(b);
+      };
+      auto place_bid = [&](int i, const Bid& b) {
+        const long long w2 = N == 1 ? b.w1 : b.w2;
+        const long long a = S.p[b.j1] + (w2 - b.w1) + eps;
+        S.obj[i] = b.j1;
+        S.amt[i] = a;
+        atomicMax(&S.best[b.j1], a);
+        if (i < n) ++real_bids;
+      };
+      if (U >= W || N < 2048) {
+        // one warp per bidder
+        for (int x = wid; x < U; x += W) {
+          const int i = S.list[x];
+          const Bid b = scan(i, lane, 32);
+          if (lane == 0) place_bid(i, b);
         }
-        if (i < n && lane == 0) ++real_bids;
+      } else {
+        // fewer bidders than warps (the late rounds) on long rows: G warps
+        // per bidder split its row, and one thread merges their partial bids
+        // (the merge is associative, so the bid is the same as one warp's)
+        int G = 1;
+        while (2 * G * U <= W) G *= 2;
+        const int x = wid / G, gw = wid % G;
+        if (x < U) {
+          const Bid b = scan(S.list[x], 32 * gw + lane, 32 * G);
+          if (lane == 0) S.part[wid] = b;
+        }
+        __syncthreads();
+        if (tid < U) {
+          Bid b = S.part[tid * G];
+          for (int q = 1; q < G; ++q) b = merge(b, S.part[tid * G + q]);
+          place_bid(S.list[tid], b);
+        }
       }
       __syncthreads();
       for (int x = tid; x < U; x += T) {
@@ -270,8 +299,8 @@ __device__ __forceinline__ void auction_instance(const Instance& I, const Auctio
     for (int i = tid; i < n; i += T) I.u[i] = 0;
   if (I.v)
     for (int j = tid; j < N; j += T) I.v[j] = 0;
-  // per-warp counters: real_bids was counted by lane 0 of each warp
-  const long long rb = block_sum<T>(lane == 0 ? real_bids : 0, S.red);
+  // real_bids was counted by the threads that placed bids
+  const long long rb = block_sum<T>(real_bids, S.red);
   const long long cost = block_sum<T>(part, S.red);
   if (tid == 0) {
     *I.cost = cost;
@@ -293,9 +322,8 @@ __device__ __forceinline__ void auction_instance(const Instance& I, const Auctio
 }
 
 template <int T>
-__global__ void __launch_bounds__(T) auction_kernel(const Instance* __restrict__ insts,
-                                                    const int32_t* __restrict__ order, int num, int* work,
-                                                    int mmax) {
+__device__ __forceinline__ void auction_loop(const Instance* __restrict__ insts, const int32_t* __restrict__ order,
+                                             int num, int* work, int mmax) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const AuctionSmem S = carve_auction(smem_raw, mmax);
   for (;;) {
@@ -309,10 +337,31 @@ __global__ void __launch_bounds__(T) auction_kernel(const Instance* __restrict__
   }
 }
 
+// Register budgets (measured): below 512 threads the compiler's choice for
+// the block size alone (several CTAs per SM for small instances); at 512 a
+// one-CTA-per-SM budget (the prices and bids of m = 4096 fill the shared
+// memory anyway), which avoids spills in the bid scan.
+template <int T>
+__global__ void __launch_bounds__(T) auction_kernel(const Instance* __restrict__ insts,
+                                                    const int32_t* __restrict__ order, int num, int* work,
+                                                    int mmax) {
+  auction_loop<T>(insts, order, num, work, mmax);
+}
+
+__global__ void __launch_bounds__(512, 1) auction_kernel_wide(const Instance* __restrict__ insts,
+                                                              const int32_t* __restrict__ order, int num,
+                                                              int* work, int mmax) {
+  auction_loop<512>(insts, order, num, work, mmax);
+}
+
 template <int T>
 cudaError_t launch_auction_t(const Instance* insts, const int32_t* order, int num, int* work, int mmax,
                              cudaStream_t stream) {
-  auto kern = auction_kernel<T>;
+  void (*kern)(const Instance*, const int32_t*, int, int*, int) = nullptr;
+  if constexpr (T >= 512)
+    kern = auction_kernel_wide;
+  else
+    kern = auction_kernel<T>;
   const size_t smem = auction_bytes(mmax);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
