@@ -311,10 +311,12 @@ __device__ __forceinline__ void solve_instance_v(const Instance& I, const GroupS
           }
         }
       }
-      ++steps;
-      rows += L;
-      bytes += 4LL * L * (m - tcount);
-      read_bytes += (pk ? 2LL : 4LL) * L * (m - tcount);
+      if constexpr (ALGO == kAlgoBKM) {
+        ++steps;
+        rows += L;
+        bytes += 4LL * L * (m - tcount);
+        read_bytes += (pk ? 2LL : 4LL) * L * (m - tcount);
+      }
 
       // A2 / B4: minimum distance outside T, lowest column on ties
       BestT<V> b{kInfV, INT_MAX};
@@ -369,6 +371,16 @@ __device__ __forceinline__ void solve_instance_v(const Instance& I, const GroupS
           }
         }
         group_sync<TPI>();
+        // KM counters once per phase: step s of the phase scanned one row
+        // over m - s columns, s = 0 .. tcount
+        {
+          const long long S = tcount + 1;
+          const long long cols = S * m - S * (S - 1) / 2;
+          steps += S;
+          rows += S;
+          bytes += 4 * cols;
+          read_bytes += (pk ? 2 : 4) * cols;
+        }
         ++matched;
         ++augs;
         break;
