@@ -244,7 +244,9 @@ int ot_serving_counters(ot_ctx* ctx, int64_t* out8);
  * that bucket and algorithm in the context's table (also appended to
  * cfg->tune_file when one was given); with algo = OT_AUTO both algorithms
  * are timed and the faster becomes the bucket's OT_AUTO choice.  Results are
- * written to scratch and discarded.  Returns OT_OK or an error code. */
+ * written to scratch and discarded.  Synchronises the device first (the
+ * instances may still be in flight on any stream).  Returns OT_OK or an
+ * error code. */
 int ot_autotune(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* ldc,
                 const int32_t* n, const int32_t* m, int32_t algo, int32_t repeats);
 
