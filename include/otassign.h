@@ -196,8 +196,9 @@ typedef struct ot_launch_info {
 
 /* Synchronises, then describes the group- and auction-engine launches of
  * the most recent solve call (instances handed to the cluster engine are
- * not listed): *count receives their number, out[0 .. min(count, max)-1]
- * their descriptions. */
+ * not listed, nor are the launches of a large host-pointer batch staged in
+ * chunks): *count receives their number, out[0 .. min(count, max)-1] their
+ * descriptions. */
 int ot_last_call_launches(ot_ctx* ctx, ot_launch_info* out, int32_t max, int32_t* count);
 
 /* Solve k independent instances in one launch set (multi-instance
