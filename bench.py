@@ -630,8 +630,10 @@ def main():
             "step_ms": {"min": min(step_ms), "median": float(np.median(step_ms)), "max": max(step_ms)},
         }
 
-    if rank == 0 and not args.skip_extras:
-        # plain one-instance-per-launch GPU KM on a sample of the same instances
+    if rank == 0 and not args.skip_extras and world == 1:
+        # side measurements at N = 1 only (the other GPUs of a multi-GPU run
+        # are not held for them): plain one-instance-per-launch GPU KM on a
+        # sample of the same instances
         sample = dC[: args.sample]
         outs = [ot._outputs(C.shape[0], C.shape[1], dev) for C in sample]
         for C, o in zip(sample[:8], outs[:8]):

@@ -329,6 +329,30 @@ def test_host_slab_batch_pipelined(oracle_mod, ctx, mode):
     assert st["launches"] >= 1
 
 
+def test_last_call_counters_and_launches(oracle_mod, ctx):
+    """ot_last_call_stats sums the oracle's KM counters over the instances of
+    the last batched call; ot_last_call_launches lists one entry per bucket
+    kernel whose instance counts add up to the batch, with device times."""
+    mats = [W.embedding_costs(n, seed=n) for n in (20, 33, 70, 130, 250, 250)]
+    b = ot.ot_assign_solve_batched(ctx, [torch.from_numpy(C).cuda() for C in mats], ot.OT_KM)
+    st = ot.ot_last_call_stats(ctx)
+    launches = ot.ot_last_call_launches(ctx)
+    want_steps = want_bytes = 0
+    for C in mats:
+        *_, s0 = oracle_mod.km(C, stats=True)
+        want_steps += s0["steps"]
+        want_bytes += s0["bytes"]
+    assert st["steps"] == want_steps
+    assert st["cost_bytes"] == want_bytes
+    assert 0 < st["read_bytes"] <= st["cost_bytes"]
+    assert sum(L["instances"] for L in launches) == len(mats)
+    assert all(L["algo"] == ot.OT_KM and L["ms"] > 0 for L in launches)
+    assert sum(L["read_bytes"] for L in launches) == st["read_bytes"]
+    assert st["launches"] == len(launches) + 1  # the bucket kernels and the packing pass
+    for t, C in enumerate(mats):
+        assert int(b.cost[t]) == oracle_mod.km(C)[1]
+
+
 def test_serving_results_equal_solo(oracle_mod, ctx):
     """Requests submitted while others run are admitted and solved in
     overlapping waves; every result equals the solo solve bit for bit."""

@@ -144,3 +144,22 @@ def test_large_fixed_iterations(sk, ctx):
     tol = dual_tol(C, eta, f0, g0, 3)
     assert np.abs(f - f0).max() <= tol and np.abs(g - g0).max() <= tol
     assert abs(cost - c0) <= 2 * tol * c0
+
+
+def test_host_outputs_and_default_stream(sk, ctx):
+    """f and g may be host arrays (raw C-ABI call); the NULL stream is the
+    caller's default stream."""
+    import ctypes
+    C = W.uniform_costs(64, 80, hi=200, seed=14)
+    Cd = torch.from_numpy(C).cuda()
+    f = np.zeros(64, np.float32)
+    g = np.zeros(80, np.float32)
+    cost, res, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    P = lambda a: ctypes.c_void_p(a.ctypes.data)
+    rc = ctx.lib.ot_sinkhorn_solve(ctx.h, ctypes.c_void_p(Cd.data_ptr()), 80, 64, 80, None, None, 0.05, 0.0, 7,
+                                   P(f), P(g), ctypes.byref(cost), ctypes.byref(res), ctypes.byref(it), None)
+    assert rc == 0 and it.value == 7
+    f0, g0, c0, _, _ = sk.sinkhorn(C, 0.05, max_iter=7, check=False)
+    tol = dual_tol(C, 0.05, f0, g0, 7)
+    assert np.abs(f - f0).max() <= tol and np.abs(g - g0).max() <= tol
+    assert abs(cost.value - c0) <= 2 * tol * c0
