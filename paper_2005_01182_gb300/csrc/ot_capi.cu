@@ -231,6 +231,15 @@ struct Bucket {
   std::vector<int> idx;
 };
 
+// 16-bit row packing for group-engine instances (OT_PACK=0 disables it).
+static bool packing_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("OT_PACK");
+    return !(e && std::atoi(e) == 0);
+  }();
+  return on;
+}
+
 // insts[t] already holds device pointers; entries with skip[t] set are not
 // launched.  Writes per-instance stats into ctx->d_stats (k x 8).
 int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts,
@@ -294,11 +303,7 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
     b.mmax = std::max(b.mmax, I.m);
     b.idx.push_back(t);
   }
-  // 16-bit row packing for the group-engine instances (OT_PACK=0 disables)
-  static const bool pack_on = [] {
-    const char* e = std::getenv("OT_PACK");
-    return !(e && std::atoi(e) == 0);
-  }();
+  const bool pack_on = packing_enabled();
   bool any_pack = false;
   if (pack_on && slot.pack && !buckets.empty()) {
     size_t nrows = 0, nelem = 0;
@@ -1079,6 +1084,28 @@ int ot_autotune(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* 
   std::map<int, std::vector<int>> byb;
   for (int t = 0; t < k; ++t)
     if (n[t] > 0 && m[t] <= kMaxGroupCols) byb[bucket_of(m[t])].push_back(t);
+  // time what the solves run: rows packed to 16 bits (and the 32-bit path)
+  // whenever the batched launches pack them
+  bool packed = false;
+  if (packing_enabled()) {
+    size_t nrows = 0, nelem = 0;
+    for (auto& kv : byb)
+      for (int t : kv.second) { nrows += size_t(n[t]); nelem += size_t(n[t]) * m[t]; }
+    const size_t b_pok = al256(sizeof(int32_t) * k), b_roff = al256(sizeof(int32_t) * nrows);
+    if (nelem > 0 && ctx->api.d_pack.reserve(b_pok + b_roff + al256(2 * nelem)) == OT_OK) {
+      char* base = static_cast<char*>(ctx->api.d_pack.ptr);
+      size_t orow = 0, oel = 0;
+      for (auto& kv : byb)
+        for (int t : kv.second) {
+          insts[t].pok = reinterpret_cast<int32_t*>(base) + t;
+          insts[t].roff = reinterpret_cast<int32_t*>(base + b_pok) + orow;
+          insts[t].P = reinterpret_cast<uint16_t*>(base + b_pok + b_roff) + oel;
+          orow += size_t(n[t]);
+          oel += size_t(n[t]) * m[t];
+        }
+      packed = true;
+    }
+  }
   cudaStream_t s = ctx->stream;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -1092,6 +1119,9 @@ int ot_autotune(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* 
   int32_t* dorder = reinterpret_cast<int32_t*>(dm + desc_bytes);
   int* dwork = reinterpret_cast<int*>(dm + desc_bytes + al256(4 * size_t(k)));
   cudaMemcpyAsync(dinst, insts.data(), sizeof(Instance) * k, cudaMemcpyHostToDevice, s);
+  if (packed) {
+    if (cudaError_t e = launch_pack(dinst, nullptr, k, s); e != cudaSuccess) return ctx_cuda(ctx, e, "autotune pack");
+  }
   FILE* tf = ctx->tune_file.empty() ? nullptr : std::fopen(ctx->tune_file.c_str(), "a");
   for (auto& kv : byb) {
     std::vector<int>& idx = kv.second;
