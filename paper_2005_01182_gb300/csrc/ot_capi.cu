@@ -689,7 +689,7 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
       cudaStreamWaitEvent(cs, ctx->hev_copy[c], 0);
       std::vector<Instance> ci(insts.begin() + bound[c], insts.begin() + bound[c + 1]);
       std::vector<int> cskip(skip.begin() + bound[c], skip.begin() + bound[c + 1]), cun;
-      if (int rc = run_device_batch(ctx, ctx->hslots[c], ci, cskip, algo, cs, false, false, &cun, route_wide); rc)
+      if (int rc = run_device_batch(ctx, ctx->hslots[c], ci, cskip, algo, cs, true, false, &cun, route_wide); rc)
         return rc;
       for (int x : cun) unsup.push_back(bound[c] + x);
       launches += ctx->hslots[c].last_launches;
