@@ -63,7 +63,7 @@ extern "C" {
 #define OT_ERR_TIMEOUT (-4)      /* a bounded device wait expired */
 #define OT_ERR_CUDA (-5)         /* a CUDA runtime call failed */
 #define OT_ERR_OVERFLOW (-6)     /* |C| too large for exact int64 duals */
-#define OT_ERR_UNSUPPORTED (-7)  /* size outside what this build handles */
+#define OT_ERR_UNSUPPORTED (-7)  /* size or option the library does not support */
 #define OT_ERR_TICKET (-8)       /* unknown or already collected ticket */
 
 #define OT_KM 0

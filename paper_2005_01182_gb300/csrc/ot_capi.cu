@@ -103,7 +103,7 @@ namespace {
 using PtrAttrsFn = CUresult (*)(unsigned int, CUpointer_attribute*, void**, CUdeviceptr);
 
 // cuPointerGetAttributes through the runtime's driver entry point (no link
-// against the driver library); null if unavailable.
+// against the CUDA driver API library); null if unavailable.
 PtrAttrsFn ptr_attrs_fn() {
   static const PtrAttrsFn fn = [] {
     void* f = nullptr;
@@ -150,7 +150,7 @@ bool PtrKinds::on_device(const void* p) {
       return dev;
     }
   }
-  return ptr_on_device(p);  // memory the driver does not track (pageable host)
+  return ptr_on_device(p);  // memory CUDA does not track (pageable host)
 }
 
 bool ptr_on_device(const void* p) {
