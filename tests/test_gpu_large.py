@@ -121,3 +121,19 @@ def gpu_solve_on(c, C, algo):
     r, cost, u, v = ot.ot_assign_solve(c, torch.from_numpy(np.ascontiguousarray(C)).cuda(), algo)
     torch.cuda.synchronize()
     return r.cpu().numpy(), int(cost.item()), u.cpu().numpy(), v.cpu().numpy()
+
+
+def test_widest_instances(oracle_mod, ctx):
+    """Few rows, very many columns: m = 30000 on the cluster engine (each
+    thread owns several columns), and a width beyond what the engine holds
+    (m = 65537) refused with OT_ERR_UNSUPPORTED before any launch."""
+    C = W.uniform_costs(3, 30000, seed=41)
+    a0, c0, u0, v0 = oracle_mod.km(C)
+    for algo in (ot.OT_KM, ot.OT_BKM):
+        a, c, u, v, _ = solve(ctx, C, algo)
+        assert c == c0
+        assert oracle_mod.check_certificate(C, a, u, v, c) == 0
+    too_wide = torch.zeros((2, 65537), dtype=torch.int32, device="cuda")
+    with pytest.raises(ot.OtError) as e:
+        ot.ot_assign_solve(ctx, too_wide, ot.OT_KM)
+    assert e.value.code == ot.OT_ERR_UNSUPPORTED
