@@ -175,6 +175,18 @@ int ot_sinkhorn_solve(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int
                       int32_t max_iter, float* f, float* g, double* cost, double* residue,
                       int32_t* iterations, void* stream);
 
+/* Log-domain Sinkhorn on k independent instances (the iteration and
+ * stopping rule of ot_sinkhorn_solve, unit marginals r = 1, c = n/m), one
+ * CTA per instance.  All pointers are device pointers: C[t] (n[t] x m[t]
+ * int32, ldc[t] >= m[t]), f[t] (n[t] floats), g[t] (m[t] floats), and the
+ * arrays cost[k], residue[k] (double) and iterations[k] (int32).
+ * Asynchronous on `stream`.  1 <= n[t], m[t] <= 4096 (OT_ERR_UNSUPPORTED
+ * above); OT_ERR_ARG for eta <= 0 or max_iter < 1. */
+int ot_sinkhorn_solve_batched(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* ldc,
+                              const int32_t* n, const int32_t* m, double eta, double eps_rel,
+                              int32_t max_iter, float* const* f, float* const* g, double* cost,
+                              double* residue, int32_t* iterations, void* stream);
+
 /* Synchronise the context's stream and return the counters of the most
  * recent ot_assign_solve / ot_assign_solve_batched call on device pointers,
  * summed over its instances; reserved[0] receives the number of kernel

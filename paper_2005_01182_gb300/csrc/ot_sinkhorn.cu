@@ -22,9 +22,11 @@
 // residue and cost accumulators.  The iteration runs until a device flag is
 // set; kernels issued after it return at once, so the host checks the flag
 // only every few iterations.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "otassign.h"
@@ -353,6 +355,132 @@ __global__ void __launch_bounds__(T) sk_col_pass(const int32_t* __restrict__ C, 
 
 constexpr int kColT = OT_SK_COL_T;
 
+// ---------------------------------------------------------------------------
+// Many small instances: one CTA iterates one instance to convergence (rows
+// and columns of up to kBatchMaxN / kBatchMaxM), the CTAs pulling instances
+// from a work counter, largest first.  Unit marginals (r = 1, c = n/m).
+// Same iteration, stopping rule and float32 arithmetic as above; f (two
+// buffers: the previous iterate is kept until its residue is known) and g
+// live in shared memory, rows are read from global memory (L2).
+// ---------------------------------------------------------------------------
+constexpr int kBatchT = 128;
+constexpr int kBatchMaxN = 4096, kBatchMaxM = 4096;
+
+struct SkInstance {
+  const int32_t* C;
+  long long ldc;
+  int n, m;
+  float* f;           // [n] output
+  float* g;           // [m] output
+  double* cost;       // output
+  double* residue;    // output
+  int* iterations;    // output
+};
+
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < kBatchT / 32; ++w) t += red[w];
+  return t;
+}
+
+__global__ void __launch_bounds__(kBatchT) sk_batch_kernel(const SkInstance* __restrict__ insts,
+                                                           const int32_t* __restrict__ order, int num, int* work,
+                                                           float eta, double eps_rel, int max_iter,
+                                                           int nmax) {
+  // f (two iterates) and g in dynamic shared memory sized for the batch
+  extern __shared__ float sk_smem[];
+  float* const gs = sk_smem + 2 * nmax;
+  __shared__ double red[2][kBatchT / 32];
+  __shared__ int sidx;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int W = kBatchT / 32;
+  for (;;) {
+    if (tid == 0) sidx = atomicAdd(work, 1);
+    __syncthreads();
+    const int idx = sidx;
+    __syncthreads();
+    if (idx >= num) break;
+    const SkInstance I = insts[order[idx]];
+    const int n = I.n, m = I.m;
+    const float logc = logf(float(n) / float(m));
+    for (int i = tid; i < n; i += kBatchT) sk_smem[i] = 0.0f;
+    for (int j = tid; j < m; j += kBatchT) gs[j] = 0.0f;
+    __syncthreads();
+    const double threshold = eps_rel > 0.0 ? eps_rel * n : -1.0;
+    int final_k = 0;
+    double res = 0.0, cost = 0.0;
+    for (int k = 1; k <= max_iter + 1; ++k) {
+      const float* f_old = sk_smem + ((k - 1) & 1) * nmax;
+      float* f_new = sk_smem + (k & 1) * nmax;
+      // row pass: f_new = -LSE_j(g - eta C); residue / cost of (f_old, g)
+      double pres = 0.0, pcost = 0.0;
+      for (int i = wid; i < n; i += W) {
+        const int32_t* row = I.C + (long long)i * I.ldc;
+        Lse a{-INFINITY, 0.0f, 0.0f};
+        for (int j0 = lane; j0 < m; j0 += 32 * 4) {
+          float x[4], c[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = j0 + 32 * u;
+            c[u] = j < m ? float(__ldg(row + j)) : 0.0f;
+            x[u] = j < m ? fmaf(-eta, c[u], gs[j]) : -INFINITY;
+          }
+          lse_chunk<4, true>(a, x, c);
+        }
+        a = warp_lse(a);
+        const float L = a.m + logf(a.s);
+        if (lane == 0) {
+          f_new[i] = -L;
+          const double fo = double(f_old[i]);
+          pres += fabs(1.0 - exp(fo + double(L)));
+          pcost += exp(fo + double(a.m)) * double(a.w);
+        }
+      }
+      res = block_sum_d(pres, red[0]);
+      cost = block_sum_d(pcost, red[1]);
+      // iterate k - 1 is returned when it meets the threshold, or when it
+      // is the last one asked for
+      if ((k >= 2 && threshold >= 0.0 && res <= threshold) || k == max_iter + 1) {
+        final_k = k - 1;
+        break;
+      }
+      __syncthreads();
+      // column pass: g_j = log(n/m) - LSE_i(f_new - eta C), one thread per column
+      for (int j = tid; j < m; j += kBatchT) {
+        Lse a{-INFINITY, 0.0f, 0.0f};
+        for (int i0 = 0; i0 < n; i0 += 4) {
+          float x[4], cz[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u;
+            x[u] = i < n ? fmaf(-eta, float(__ldg(I.C + (long long)i * I.ldc + j)), f_new[i]) : -INFINITY;
+            cz[u] = 0.0f;
+          }
+          lse_chunk<4, false>(a, x, cz);
+        }
+        gs[j] = logc - (a.m + logf(a.s));
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    const float* ff = sk_smem + (final_k & 1) * nmax;
+    for (int i = tid; i < n; i += kBatchT) I.f[i] = ff[i];
+    for (int j = tid; j < m; j += kBatchT) I.g[j] = gs[j];
+    if (tid == 0) {
+      *I.cost = cost;
+      *I.residue = res;
+      *I.iterations = final_k;
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 }  // namespace ot
 
@@ -485,5 +613,65 @@ extern "C" int ot_sinkhorn_solve(ot_ctx* ctx, const int32_t* C, int64_t ldc, int
   *cost = h.cost;
   if (residue) *residue = h.residue;
   if (iterations) *iterations = h.iterations;
+  return OT_OK;
+}
+
+extern "C" int ot_sinkhorn_solve_batched(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* ldc,
+                                         const int32_t* n, const int32_t* m, double eta, double eps_rel,
+                                         int32_t max_iter, float* const* f, float* const* g, double* cost,
+                                         double* residue, int32_t* iterations, void* stream) {
+  if (!ctx) return OT_ERR_ARG;
+  if (k < 0 || !(eta > 0.0) || !std::isfinite(eta) || max_iter < 1) return ctx_fail(ctx, OT_ERR_ARG, "bad arguments");
+  if (k == 0) return OT_OK;
+  if (!C || !ldc || !n || !m || !f || !g || !cost || !residue || !iterations)
+    return ctx_fail(ctx, OT_ERR_ARG, "null array");
+  cudaSetDevice(ctx->device);
+  std::vector<SkInstance> hi(k);
+  std::vector<int32_t> ord(k);
+  for (int t = 0; t < k; ++t) {
+    if (n[t] < 1 || m[t] < 1 || n[t] > kBatchMaxN || m[t] > kBatchMaxM || !C[t] || ldc[t] < m[t] || !f[t] || !g[t])
+      return ctx_fail(ctx, n[t] > kBatchMaxN || m[t] > kBatchMaxM ? OT_ERR_UNSUPPORTED : OT_ERR_ARG,
+                      "bad instance " + std::to_string(t));
+    hi[t] = SkInstance{C[t], ldc[t], n[t], m[t], f[t], g[t], cost + t, residue + t, iterations + t};
+    ord[t] = t;
+  }
+  if (!ptr_on_device(C[0]) || !ptr_on_device(cost)) return ctx_fail(ctx, OT_ERR_ARG, "device pointers expected");
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) {
+    const long long wa = (long long)n[a] * m[a], wb = (long long)n[b] * m[b];
+    return wa != wb ? wa > wb : a < b;
+  });
+  std::lock_guard<std::mutex> lock(ctx->scaled_mu);
+  StreamScope scope(static_cast<cudaStream_t>(stream), ctx->stream, ctx->sjoin_in_ev, ctx->sjoin_out_ev);
+  cudaStream_t s = scope.work;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t b_inst = al(sizeof(SkInstance) * k), b_ord = al(4 * size_t(k));
+  if (int rc = ctx->d_scaled.reserve(b_inst + b_ord + 256); rc) return ctx_fail(ctx, rc, "sinkhorn batch workspace");
+  char* B = static_cast<char*>(ctx->d_scaled.ptr);
+  // the pinned staging of the descriptors must outlive the asynchronous copy
+  std::vector<char> hbuf(b_inst + b_ord + 256, 0);
+  std::memcpy(hbuf.data(), hi.data(), sizeof(SkInstance) * k);
+  std::memcpy(hbuf.data() + b_inst, ord.data(), 4 * size_t(k));
+  cudaError_t e = cudaMemcpyAsync(B, hbuf.data(), b_inst + b_ord + 256, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // hbuf is pageable and local
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "sinkhorn batch setup");
+  int* dwork = reinterpret_cast<int*>(B + b_inst + b_ord);
+  if ((e = cudaMemsetAsync(dwork, 0, sizeof(int), s)) != cudaSuccess) return ctx_cuda(ctx, e, "sinkhorn batch");
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int nmax = 0, mmax = 0;
+  for (int t = 0; t < k; ++t) {
+    nmax = std::max(nmax, int(n[t]));
+    mmax = std::max(mmax, int(m[t]));
+  }
+  const size_t smem = sizeof(float) * (2 * size_t(nmax) + size_t(mmax));
+  if ((e = cudaFuncSetAttribute(sk_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) != cudaSuccess)
+    return ctx_cuda(ctx, e, "sinkhorn batch smem");
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sk_batch_kernel, kBatchT, smem);
+  const int grid = std::max(1, std::min(k, std::max(1, per_sm) * sms));
+  sk_batch_kernel<<<grid, kBatchT, smem, s>>>(reinterpret_cast<const SkInstance*>(B),
+                                              reinterpret_cast<const int32_t*>(B + b_inst), k, dwork, float(eta),
+                                              eps_rel, max_iter, nmax);
+  if ((e = cudaGetLastError()) != cudaSuccess) return ctx_cuda(ctx, e, "sinkhorn batch launch");
   return OT_OK;
 }

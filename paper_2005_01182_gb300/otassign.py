@@ -102,6 +102,9 @@ def load(path: str | None = None):
                                              i32, vp, vp, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), vp]),
         "ot_last_call_launches": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32)]),
+        "ot_sinkhorn_solve_batched": (ctypes.c_int, [vp, i32, pp, ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                                     ctypes.POINTER(i32), ctypes.c_double, ctypes.c_double, i32,
+                                                     pp, pp, vp, vp, vp, vp]),
         "ot_version": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -284,6 +287,43 @@ def ot_transport_solve(ctx: Context, C: torch.Tensor, supply, demand, algo: int 
                                     _stream_handle(stream))
     ctx._raise(rc, "ot_transport_solve")
     return flow, int(c.item())
+
+
+class SinkhornBatch:
+    """Pre-marshalled arguments of ot_sinkhorn_solve_batched (device cost
+    matrices); outputs f[t], g[t] (float32), cost, residue, iterations."""
+
+    def __init__(self, Cs):
+        k = len(Cs)
+        self.k = k
+        self.Cs = Cs
+        sizes = [_check_cost(C) for C in Cs]
+        dev = Cs[0].device
+        self.n = (ctypes.c_int32 * k)(*[s[0] for s in sizes])
+        self.m = (ctypes.c_int32 * k)(*[s[1] for s in sizes])
+        self.ldc = (ctypes.c_int64 * k)(*[s[2] for s in sizes])
+        self.cp = (ctypes.c_void_p * k)(*[C.data_ptr() for C in Cs])
+        self.f = [torch.empty(s[0], dtype=torch.float32, device=dev) for s in sizes]
+        self.g = [torch.empty(s[1], dtype=torch.float32, device=dev) for s in sizes]
+        self.fp = (ctypes.c_void_p * k)(*[x.data_ptr() for x in self.f])
+        self.gp = (ctypes.c_void_p * k)(*[x.data_ptr() for x in self.g])
+        self.cost = torch.empty(k, dtype=torch.float64, device=dev)
+        self.residue = torch.empty(k, dtype=torch.float64, device=dev)
+        self.iterations = torch.empty(k, dtype=torch.int32, device=dev)
+
+
+def ot_sinkhorn_solve_batched(ctx: Context, Cs_or_batch, eta: float, eps_rel: float = 1e-3,
+                              max_iter: int = 1000, stream=None):
+    """Log-domain Sinkhorn on many device instances, one CTA each; returns
+    the SinkhornBatch holding f, g, cost, residue, iterations."""
+    b = Cs_or_batch if isinstance(Cs_or_batch, SinkhornBatch) else SinkhornBatch(Cs_or_batch)
+    P = ctypes.cast
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    rc = ctx.lib.ot_sinkhorn_solve_batched(ctx.h, b.k, P(b.cp, pp), b.ldc, b.n, b.m, float(eta), float(eps_rel),
+                                           int(max_iter), P(b.fp, pp), P(b.gp, pp), _ptr(b.cost), _ptr(b.residue),
+                                           _ptr(b.iterations), _stream_handle(stream))
+    ctx._raise(rc, "ot_sinkhorn_solve_batched")
+    return b
 
 
 class ot_launch_info(ctypes.Structure):

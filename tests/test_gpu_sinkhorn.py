@@ -163,3 +163,50 @@ def test_host_outputs_and_default_stream(sk, ctx):
     tol = dual_tol(C, 0.05, f0, g0, 7)
     assert np.abs(f - f0).max() <= tol and np.abs(g - g0).max() <= tol
     assert abs(cost.value - c0) <= 2 * tol * c0
+
+
+def test_batched_fixed_iterations(sk, ctx):
+    """ot_sinkhorn_solve_batched: each instance equals the float64 oracle
+    within the same bound, sizes 1 x 1 to 300 x 333 in one call."""
+    rng = np.random.default_rng(15)
+    shapes = [(1, 1), (1, 5), (7, 7), (33, 40), (100, 100), (128, 200), (256, 256), (300, 333)]
+    mats = [W.uniform_costs(n, m, hi=400, seed=int(rng.integers(1 << 20))) for n, m in shapes]
+    eta, K = 0.03, 6
+    b = ot.ot_sinkhorn_solve_batched(ctx, [torch.from_numpy(C).cuda() for C in mats], eta, eps_rel=0.0, max_iter=K)
+    torch.cuda.synchronize()
+    its = b.iterations.cpu().numpy()
+    costs = b.cost.cpu().numpy()
+    for t, C in enumerate(mats):
+        f0, g0, c0, _, _ = sk.sinkhorn(C, eta, max_iter=K, check=False)
+        tol = dual_tol(C, eta, f0, g0, K)
+        assert its[t] == K
+        assert np.abs(b.f[t].cpu().numpy() - f0).max() <= tol
+        assert np.abs(b.g[t].cpu().numpy() - g0).max() <= tol
+        assert abs(costs[t] - c0) <= 2 * tol * abs(c0) + 1e-9
+
+
+def test_batched_convergence(sk, ctx):
+    mats = [W.uniform_costs(n, hi=1000, seed=n) for n in (40, 90, 200)] + [W.pixel_sqdist(150, seed=3)]
+    eta = 0.05
+    b = ot.ot_sinkhorn_solve_batched(ctx, [torch.from_numpy(C).cuda() for C in mats], eta, eps_rel=1e-3, max_iter=3000)
+    torch.cuda.synchronize()
+    for t, C in enumerate(mats):
+        n, m = C.shape
+        f0, g0, c0, it0, _ = sk.sinkhorn(C, eta, eps_rel=1e-3, max_iter=3000)
+        it = int(b.iterations[t])
+        assert abs(it - it0) <= 1
+        f = b.f[t].cpu().numpy().astype(np.float64)
+        g = b.g[t].cpu().numpy().astype(np.float64)
+        r, _ = sk.default_marginals(n, m)
+        rows, _ = sk.marginals(C, eta, f, g)
+        assert np.abs(r - rows).sum() <= 1.1e-3 * n
+        assert abs(float(b.cost[t]) - sk.transport_cost(C, eta, f, g)) <= 1e-4 * abs(float(b.cost[t]))
+
+
+def test_batched_limits(ctx):
+    big = torch.zeros((4097, 4097), dtype=torch.int32, device="cuda")
+    with pytest.raises(ot.OtError) as e:
+        ot.ot_sinkhorn_solve_batched(ctx, [big], 1.0)
+    assert e.value.code == ot.OT_ERR_UNSUPPORTED
+    with pytest.raises(ot.OtError):
+        ot.ot_sinkhorn_solve_batched(ctx, [big[:4, :4].contiguous()], 0.0)
