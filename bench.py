@@ -229,13 +229,14 @@ def run_reference(args):
 
 
 def measure_single_4096(stream, ot, torch):
-    """n = m = 4096 single solves (circle/square shapes and uniform costs):
-    KM on one CTA vs batched KM (routed to the cluster engine) vs the
+    """Single solves: n = m = 4096 (circle/square shapes and uniform costs)
+    and n = m = 256 (integer points on a 64 x 64 grid): KM on one CTA vs
+    batched KM (routed to the cluster engine above 1024 columns) vs the
     epsilon-scaling auction on one CTA, s/solve."""
     out = {}
     ctx = ot.Context()
-    for kind in ("circle-square", "uniform"):
-        Cd = torch.from_numpy(W.single_4096(kind)).cuda()
+    for kind in ("circle-square", "uniform", "grid256"):
+        Cd = torch.from_numpy(W.single_256() if kind == "grid256" else W.single_4096(kind)).cuda()
         torch.cuda.synchronize()
         res = {}
         for name, algo in (("km", ot.OT_KM), ("batched_km", ot.OT_BKM), ("auction", ot.OT_AUCTION)):
