@@ -342,9 +342,19 @@ def measure_sinkhorn_4096(stream, ot, torch):
             chosen = rec
             break
     ctx.close()
+    # the float64 oracle's cost per iteration at this size (2 iterations)
+    import oracle.sinkhorn as sko
+    C = Cd.cpu().numpy()
+    t0 = time.perf_counter()
+    sko.sinkhorn(C, 0.3, max_iter=2, check=False)
+    oracle_it = (time.perf_counter() - t0) / 2
     del Cd
     torch.cuda.empty_cache()
-    return {"opt": opt, "epsilon_rel": 1e-3, "chosen": chosen, "tried": tried}
+    gpu_it = chosen["s"] / max(1, chosen["iterations"]) if chosen else None
+    return {"opt": opt, "epsilon_rel": 1e-3, "chosen": chosen, "tried": tried,
+            "cpu_oracle": {"s_per_iteration": oracle_it, "cores": 1, "kind": "oracle",
+                           "sample": "2 iterations of the numpy float64 oracle at n = 4096"},
+            "gpu_s_per_iteration": gpu_it}
 
 
 def measure_sinkhorn_batch(ctx, dC, opt, stream, ot, torch):
@@ -372,8 +382,19 @@ def measure_sinkhorn_batch(ctx, dC, opt, stream, ot, torch):
         if ratio.max() <= 1.1:
             chosen = rec
             break
-    return {"epsilon_rel": 1e-3, "chosen": chosen, "tried": tried,
-            "note": "approximate; exact KM on the same batch is the main value"}
+    out = {"epsilon_rel": 1e-3, "chosen": chosen, "tried": tried,
+           "note": "approximate; exact KM on the same batch is the main value"}
+    if chosen is not None:
+        # the float64 oracle, single thread, on a bounded sample
+        import oracle.sinkhorn as sko
+        t0 = time.perf_counter()
+        done = 0
+        while time.perf_counter() - t0 < 3.0 and done < len(dC):
+            sko.sinkhorn(dC[done].cpu().numpy(), chosen["eta"], eps_rel=1e-3, max_iter=5000)
+            done += 1
+        out["cpu_oracle"] = {"value": done / (time.perf_counter() - t0), "unit": UNIT, "cores": 1,
+                             "sample": f"first {done} instances, numpy float64 oracle, eta {chosen['eta']}"}
+    return out
 
 
 def measure_served(ctx_unused, stream, ot, torch, dev, args):
@@ -475,12 +496,13 @@ def main():
     ap.add_argument("--skip-extras", action="store_true")
     ap.add_argument("--served-requests", type=int, default=1500)
     ap.add_argument("--profile-once", default=None,
-                    choices=["batch", "n16384", "n8192", "sinkhorn16384", "sinkhorn8192"],
+                    choices=["batch", "auction", "n16384", "n8192", "sinkhorn16384", "sinkhorn8192"],
                     help="untimed single run for an ncu capture: 'batch' = autotune, then 3 batched "
                          "OT_AUTO calls on the 4096-instance batch inside an NVTX range 'timed'; "
                          "'n16384' / 'n8192' = one batched-KM solve on a grid instance; "
                          "'sinkhorn16384' / 'sinkhorn8192' = log-domain Sinkhorn, eta = 2, 3 / 2 "
-                         "fixed iterations on a 1024 x 1024-grid instance")
+                         "fixed iterations on a 1024 x 1024-grid instance; 'auction' = one OT_AUCTION "
+                         "solve of the 4096-instance batch inside an NVTX range 'timed'")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -528,6 +550,17 @@ def main():
         return
     Cs = batch_for_rank(rank, args.k)
     dC = [torch.from_numpy(C).to(dev) for C in Cs]
+    if args.profile_once == "auction":
+        a = ot.BatchArgs(dC)
+        ot.ot_assign_solve_batched(ctx, a, ot.OT_AUCTION, stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
+        ot.ot_assign_solve_batched(ctx, a, ot.OT_AUCTION, stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        assert (a.status.cpu().numpy() == 0).all()
+        ctx.close()
+        return
     if args.profile_once:
         # the timed configuration: tuned table, OT_AUTO; the three calls sit
         # in an NVTX range "timed" for ncu --nvtx-include
@@ -693,10 +726,25 @@ def main():
         ast = ot.ot_last_call_stats(ctx)
         assert (args_auc.status.cpu().numpy() == 0).all()
         assert (args_auc.cost.cpu().numpy() == args_dev.cost.cpu().numpy()).all(), "auction cost differs from KM"
-        line["auction"] = {"value": 3 * len(dC) / (a0.elapsed_time(a1) / 1000.0), "unit": UNIT,
-                           "ms_per_step": a0.elapsed_time(a1) / 3, "bids": ast["rows_scanned"],
+        auc_s = a0.elapsed_time(a1) / 3000.0
+        auc_bytes = ast["cost_bytes"] + ast["init_bytes"]
+        peak_a, _ = _peaks()
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        done = 0
+        while time.perf_counter() - t0 < 3.0 and done < len(Cs):
+            oracle.auction(Cs[done])
+            done += 1
+        oracle_rate = done / (time.perf_counter() - t0)
+        line["auction"] = {"value": len(dC) / auc_s, "unit": UNIT,
+                           "ms_per_step": auc_s * 1000.0, "bids": ast["rows_scanned"],
                            "rounds": ast["steps"], "stages": ast["phases"],
-                           "note": "same 4096 instances, OT_AUCTION, costs equal to KM's"}
+                           "algorithmic_bytes": auc_bytes, "achieved_gbs": auc_bytes / auc_s / 1e9,
+                           "hbm_frac": auc_bytes / auc_s / 1e9 / peak_a,
+                           "cpu_oracle": {"value": oracle_rate, "unit": UNIT, "cores": 1,
+                                          "sample": f"first {done} instances, oracle auction, single thread"},
+                           "note": "same 4096 instances, OT_AUCTION, costs equal to KM's; bound: round latency"}
         del args_auc
         line["sinkhorn_batch"] = measure_sinkhorn_batch(ctx, dC, args_dev.cost.cpu().numpy(), stream, ot, torch)
         cores = host_threads()
