@@ -815,12 +815,11 @@ int ot_ctx_create(ot_ctx** out, const ot_config* cfg) {
   ot_config c{};
   c.device = -1;
   if (cfg) c = *cfg;
-  cudaError_t e;
   if (c.device >= 0) {
-    if ((e = cudaSetDevice(c.device)) != cudaSuccess) { delete ctx; return OT_ERR_CUDA; }
+    if (cudaSetDevice(c.device) != cudaSuccess) { delete ctx; return OT_ERR_CUDA; }
     ctx->device = c.device;
   } else {
-    if ((e = cudaGetDevice(&ctx->device)) != cudaSuccess) { cudaGetLastError(); delete ctx; return OT_ERR_CUDA; }
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) { cudaGetLastError(); delete ctx; return OT_ERR_CUDA; }
   }
   if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { delete ctx; return OT_ERR_CUDA; }
   for (int i = 0; i < kForkStreams; ++i) {
@@ -855,7 +854,7 @@ int ot_ctx_create(ot_ctx** out, const ot_config* cfg) {
     load_tune_file(ctx);
   }
   if (int rc = serve_init(ctx, c); rc) { ot_ctx_destroy(ctx); return rc; }
-  if ((e = cudaGetLastError()) != cudaSuccess) { ot_ctx_destroy(ctx); return OT_ERR_CUDA; }
+  if (cudaGetLastError() != cudaSuccess) { ot_ctx_destroy(ctx); return OT_ERR_CUDA; }
   *out = ctx;
   return OT_OK;
 }

@@ -34,9 +34,6 @@
 
 // Launch shape of the two passes (compile-time; the defaults are the ones
 // measured best on GB300 for n = m = 16384).
-#ifndef OT_SK_ROW_UNROLL
-#define OT_SK_ROW_UNROLL 4
-#endif
 #ifndef OT_SK_ROW_MINB
 #define OT_SK_ROW_MINB 1
 #endif
@@ -53,7 +50,6 @@
 namespace ot {
 namespace {
 
-constexpr int kRowUnroll = OT_SK_ROW_UNROLL;
 constexpr int kColUnroll = OT_SK_COL_UNROLL;
 
 struct SkState {
