@@ -15,6 +15,8 @@ What each function follows in the paper:
   * ``bkm``          -- batched KM, exact mode (Sec. 2.3 "Batched KM").
   * ``check_certificate`` -- LP duality for Eq. 1 (weak duality makes a
     feasible dual with equal objective a proof of optimality).
+  * ``transport``    -- integer-supply transport (Eq. 1, Sec. 2) by vertex
+    replication onto ``km``.
   * ``auction``      -- the auction algorithm with epsilon-scaling in
     parallel (Jacobi) rounds (Sec. 2.3.3 "The auction algorithm", Sec. 4.1
     "Auction"), exact for integer costs by scaling them by N + 1 and
@@ -155,6 +157,29 @@ def auction(C, stats: bool = False):
         return out + ({"stages": int(st[0]), "rounds": int(st[1]), "bids": int(st[2]),
                        "real_bids": int(st[3])},)
     return out
+
+
+def transport(C, supply, demand):
+    """Integer-supply transport (Eq. 1 with integer r and c, the
+    Hitchcock-Koopmans case of Sec. 2) by vertex replication: row i is
+    repeated supply[i] times and column j demand[j] times, in index order,
+    ``km`` solves the replicated assignment problem, and the flow counts the
+    copies of row i matched to copies of column j.  Demands are capacities:
+    sum(supply) <= sum(demand).  Returns (flow int64 n x m, cost)."""
+    C = np.ascontiguousarray(C, dtype=np.int32)
+    r = np.asarray(supply, dtype=np.int64)
+    c = np.asarray(demand, dtype=np.int64)
+    n, m = C.shape
+    if r.shape != (n,) or c.shape != (m,) or (r < 0).any() or (c < 0).any() or r.sum() > c.sum():
+        raise ValueError("need nonnegative supplies and demands with sum(supply) <= sum(demand)")
+    rows = np.repeat(np.arange(n), r)
+    cols = np.repeat(np.arange(m), c)
+    flow = np.zeros((n, m), np.int64)
+    if len(rows) == 0:
+        return flow, 0
+    a, cost, _, _ = km(C[np.ix_(rows, cols)])
+    np.add.at(flow, (rows, cols[a]), 1)
+    return flow, int(cost)
 
 
 def brute_force(C):

@@ -20,6 +20,8 @@ them with the same shapes and cost structure:
                        round(1e4 * Euclidean distance) in FP64 (NLP-like).
 * ``pixel_sqdist``  -- random pixel positions (with replacement) on a 28 x 28
                        grid, cost = squared distance (MNIST-like, many ties).
+* ``mnist_transport`` -- two images of distinct nonzero pixels with integer
+                       intensities of equal totals (integer-supply transport).
 
 Every generator takes an explicit integer seed (numpy PCG64); the batch and
 serving streams derive per-instance seeds as ``base + index``.
@@ -124,6 +126,31 @@ def pixel_sqdist(n: int, m: int | None = None, side: int = 28, seed: int = BASE_
     a = np.stack([pa // side, pa % side], 1)
     b = np.stack([pb // side, pb % side], 1)
     return _sqdist_int(a, b)
+
+
+def mnist_transport(n: int, m: int, total: int, side: int = 28, seed: int = BASE_SEED):
+    """Two 'images' for integer-supply transport (MNIST-like, Table 1): n and
+    m distinct nonzero pixels of a side x side grid, C = squared distance,
+    and integer intensities (at least 1 per pixel) summing to `total` on both
+    sides, drawn as uniform weights and rounded by largest remainder.
+    Returns (C, supply, demand)."""
+    r = _rng(seed)
+    pa = r.choice(side * side, size=n, replace=False)
+    pb = r.choice(side * side, size=m, replace=False)
+    a = np.stack([pa // side, pa % side], 1)
+    b = np.stack([pb // side, pb % side], 1)
+
+    def weights(k):
+        if total < k:
+            raise ValueError("total must cover one unit per pixel")
+        w = r.uniform(0.05, 1.0, size=k)
+        x = (total - k) * w / w.sum()
+        q = np.floor(x).astype(np.int64)
+        rest = int(total - k - q.sum())
+        q[np.argsort(q - x)[:rest]] += 1  # largest remainders first
+        return (q + 1).astype(np.int32)
+
+    return _sqdist_int(a, b), weights(n), weights(m)
 
 
 # ---------------------------------------------------------------------------

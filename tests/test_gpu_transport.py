@@ -60,3 +60,30 @@ def test_transport_mnist_like(ctx):
     X = flow.cpu().numpy()
     np.testing.assert_array_equal(X.sum(1), r)
     assert cost == _lp(C, r, c)
+
+
+def test_transport_km_flow_matches_oracle(ctx, oracle_mod):
+    """Through KM on the replicated matrix (rows and columns repeated in
+    index order on both sides) the flow is the oracle's, entry for entry;
+    batched KM and the automatic choice reach the same cost."""
+    cases = [W.mnist_transport(40, 45, 300, seed=5), W.mnist_transport(116, 169, 700, seed=6)]
+    rng = np.random.default_rng(17)
+    for _ in range(4):
+        n, m = int(rng.integers(1, 30)), int(rng.integers(1, 30))
+        r = rng.integers(0, 9, n).astype(np.int32)
+        c = rng.integers(0, 11, m).astype(np.int32)
+        if r.sum() > c.sum():
+            c[-1] += r.sum() - c.sum()
+        cases.append((rng.integers(-300, 300, size=(n, m)).astype(np.int32), r, c))
+    for C, r, c in cases:
+        f0, c0 = oracle_mod.transport(C, r, c)
+        Cd = torch.from_numpy(C).cuda()
+        flow, cost = ot.ot_transport_solve(ctx, Cd, r, c, ot.OT_KM)
+        assert cost == c0
+        np.testing.assert_array_equal(flow.cpu().numpy(), f0)
+        for algo in (ot.OT_BKM, ot.OT_AUTO):
+            flow, cost = ot.ot_transport_solve(ctx, Cd, r, c, algo)
+            X = flow.cpu().numpy().astype(np.int64)
+            assert cost == c0 and int((X * C).sum()) == c0
+            np.testing.assert_array_equal(X.sum(1), r)
+            assert (X.sum(0) <= c).all()

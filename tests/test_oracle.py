@@ -295,9 +295,17 @@ def _transport_lp(C, r, c):
     return int(round(res.fun))
 
 
+def _check_flow(C, r, c, flow, cost):
+    assert (flow >= 0).all()
+    np.testing.assert_array_equal(flow.sum(1), r)
+    assert (flow.sum(0) <= c).all()
+    assert int((flow * C.astype(np.int64)).sum()) == cost
+
+
 def test_transport_by_replication(oracle_mod):
     """Vertex replication turns integer-supply transport (Eq. 1) into an
-    assignment problem with the same optimum (checked against an LP)."""
+    assignment problem with the same optimum: the folded flow is feasible,
+    costs what the oracle reports, and that cost equals an LP optimum."""
     rng = np.random.default_rng(31)
     for trial in range(40):
         n, m = int(rng.integers(1, 6)), int(rng.integers(1, 7))
@@ -306,10 +314,38 @@ def test_transport_by_replication(oracle_mod):
         if r.sum() > c.sum():
             c[0] += r.sum() - c.sum()
         C = rng.integers(-20, 100, size=(n, m)).astype(np.int32)
-        rows = np.repeat(np.arange(n), r)
-        cols = np.repeat(np.arange(m), c)
-        if len(rows) == 0:
-            continue
-        rep = C[np.ix_(rows, cols)]
-        cost = oracle_mod.km(rep)[1]
-        assert cost == _transport_lp(C, r, c)
+        flow, cost = oracle_mod.transport(C, r, c)
+        _check_flow(C, r, c, flow, cost)
+        if r.sum() > 0:
+            assert cost == _transport_lp(C, r, c)
+        else:
+            assert cost == 0 and not flow.any()
+
+
+def test_transport_closed_forms(oracle_mod):
+    """One source fills the cheapest columns first (a greedy optimum); one
+    sink takes every unit; unit supplies and demands give the assignment."""
+    rng = np.random.default_rng(37)
+    for trial in range(30):
+        m = int(rng.integers(1, 9))
+        C = rng.integers(0, 50, size=(1, m)).astype(np.int32)
+        c = rng.integers(0, 4, m)
+        s = int(rng.integers(0, c.sum() + 1))
+        left, best = s, 0
+        for j in np.argsort(C[0], kind="stable"):
+            take = min(left, int(c[j]))
+            best += take * int(C[0, j])
+            left -= take
+        flow, cost = oracle_mod.transport(C, [s], c)
+        _check_flow(C, [s], c, flow, cost)
+        assert cost == best
+        n = int(rng.integers(1, 6))
+        C1 = rng.integers(-30, 30, size=(n, 1)).astype(np.int32)
+        r1 = rng.integers(0, 4, n)
+        flow, cost = oracle_mod.transport(C1, r1, [int(r1.sum()) + int(rng.integers(0, 3))])
+        assert cost == int((C1[:, 0].astype(np.int64) * r1).sum())
+        k = int(rng.integers(1, 7))
+        Ck = rng.integers(0, 100, size=(k, k + 1)).astype(np.int32)
+        flow, cost = oracle_mod.transport(Ck, np.ones(k, int), np.ones(k + 1, int))
+        assert cost == oracle_mod.brute_force(Ck)[1]
+        assert (flow.sum(0) <= 1).all()
