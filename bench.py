@@ -232,7 +232,9 @@ def measure_single_4096(stream, ot, torch):
     """Single solves: n = m = 4096 (circle/square shapes and uniform costs)
     and n = m = 256 (integer points on a 64 x 64 grid): KM on one CTA vs
     batched KM (routed to the cluster engine above 1024 columns) vs the
-    epsilon-scaling auction on one CTA, s/solve."""
+    epsilon-scaling auction on one CTA, s/solve; on circle/square also the
+    single-scaling-factor variant (s = 16) and the oracle's KM and scaled
+    batched KM beside them."""
     out = {}
     ctx = ot.Context()
     for kind in ("circle-square", "uniform", "grid256"):
@@ -250,6 +252,25 @@ def measure_single_4096(stream, ot, torch):
                 t = e0.elapsed_time(e1) / 1000.0
                 best = t if best is None else min(best, t)
             res[name] = {"s_per_solve": best, "cost": int(c.item()), "steps": st["steps"]}
+        if kind == "circle-square":
+            # the single-scaling-factor variant (s = 16) and the oracle beside both
+            import oracle
+            C = Cd.cpu().numpy()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r, c, bound = ot.ot_assign_solve_scaled(ctx, Cd, 16, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res["scaled_batched_km_s16"] = {"s_per_solve": e0.elapsed_time(e1) / 1000.0, "cost": int(c.item()),
+                                            "bound": bound}
+            t0 = time.perf_counter()
+            _, c_km, _, _ = oracle.km(C)
+            t_km = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            oracle.bkm(np.floor_divide(C, 16).astype(np.int32))
+            t_sc = time.perf_counter() - t0
+            res["cpu_oracle"] = {"km_s_per_solve": t_km, "cost": c_km, "scaled_batched_km_s16_s_per_solve": t_sc,
+                                 "cores": 1, "kind": "oracle", "sample": "one solve each, single thread"}
         out[kind] = res
     ctx.close()
     return out

@@ -1,5 +1,7 @@
 """GPU parity of the cluster engine (instances wider than one CTA, m > 4096,
 and smaller buckets routed to it on purpose) against the CPU oracle."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -84,9 +86,22 @@ def test_wide_instances(oracle_mod, ctx):
     assert c == oracle_mod.km(C)[1]
 
 
+def oracle_cost(name):
+    """The CPU oracle's optimal cost of a named workload, stored by
+    tests/golden/make_oracle_costs.py (None when not stored)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_costs.txt")
+    if os.path.exists(path):
+        for line in open(path):
+            f = line.split()
+            if f and not line.startswith("#") and f[0] == name:
+                return int(f[1])
+    return None
+
+
 def test_single_16384(oracle_mod, ctx):
     """n = m = 16384 on a 1024 x 1024 grid: batched KM certified on the host
-    (O(n^2) dual check) and equal to the cluster engine's KM cost."""
+    (O(n^2) dual check), equal to the cluster engine's KM cost and to the
+    oracle's stored optimum."""
     C = W.single_16384()
     a, c, u, v, st = solve(ctx, C, ot.OT_BKM)
     assert oracle_mod.check_certificate(C, a, u, v, c) == 0
@@ -94,6 +109,21 @@ def test_single_16384(oracle_mod, ctx):
     a2, c2, u2, v2, _ = solve(ctx, C, ot.OT_KM)
     assert c2 == c
     assert oracle_mod.check_certificate(C, a2, u2, v2, c2) == 0
+    stored = oracle_cost("single_16384_grid")
+    assert stored is None or stored == c
+
+
+@pytest.mark.parametrize("kind", ["circle-square", "uniform"])
+def test_single_4096_matches_stored_oracle_cost(ctx, kind):
+    """n = 4096 single solves (both engines, KM and batched KM) against the
+    oracle's stored optimum."""
+    stored = oracle_cost("single_4096_" + kind.replace("-", "_"))
+    if stored is None:
+        pytest.skip("no stored oracle cost")
+    C = W.single_4096(kind)
+    for algo in (ot.OT_KM, ot.OT_BKM, ot.OT_AUCTION):
+        _, c, _, _, _ = solve(ctx, C, algo)
+        assert c == stored
 
 
 def test_wide_single_batched_km_takes_the_cluster_engine(oracle_mod):
