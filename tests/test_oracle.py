@@ -349,3 +349,18 @@ def test_transport_closed_forms(oracle_mod):
         flow, cost = oracle_mod.transport(Ck, np.ones(k, int), np.ones(k + 1, int))
         assert cost == oracle_mod.brute_force(Ck)[1]
         assert (flow.sum(0) <= 1).all()
+
+
+def test_stored_oracle_costs_reproduce(oracle_mod):
+    """tests/golden/oracle_costs.txt holds the oracle's optima of the large
+    named workloads (written by tests/golden/make_oracle_costs.py); the
+    cheapest entry is recomputed here, so the file cannot drift from the
+    oracle unnoticed."""
+    from paper_2005_01182_gb300 import workloads as W
+    stored = {}
+    for line in open(os.path.join(HERE, "golden", "oracle_costs.txt")):
+        f = line.split()
+        if f and not line.startswith("#"):
+            stored[f[0]] = int(f[1])
+    assert set(stored) == {"single_4096_circle_square", "single_4096_uniform", "single_16384_grid"}
+    assert oracle_mod.km(W.single_4096("uniform"))[1] == stored["single_4096_uniform"]
