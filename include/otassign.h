@@ -139,7 +139,8 @@ int ot_assign_solve_scaled(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n
 /* Optimal transport with integer supplies and demands (Sec. 1, Eq. 1:
  * min <C, X> subject to X 1 = r, X^T 1 = c with nonnegative integer r, c),
  * solved exactly by vertex replication: row i is copied supply[i] times and
- * column j demand[j] times, the R x M assignment problem (R = sum(supply) <=
+ * column j demand[j] times (copies in index order, so that OT_KM returns a
+ * deterministic flow), the R x M assignment problem (R = sum(supply) <=
  * M = sum(demand)) is solved with `algo`, and flow[i*m + j] counts the
  * matched copies of (i, j).  With equal totals this is Eq. 1; with
  * R < M every column receives at most demand[j].  *cost = <C, X>.  Only
