@@ -39,4 +39,4 @@ def test_mnist_transport_totals_and_pixels():
     # distinct pixels per image: two pixels of one image at the same place
     # would give two identical rows (or columns) of distances
     C, _, _ = W.mnist_transport(116, 169, 2048, seed=9)
-    assert len(np.unique(C, axis=0)) == 116 and len(np.unique(C, axis=1)) == 169
+    assert np.unique(C, axis=0).shape[0] == 116 and np.unique(C, axis=1).shape[1] == 169
