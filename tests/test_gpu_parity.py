@@ -184,6 +184,13 @@ def test_bad_arguments(ctx):
     assert e.value.code == ot.OT_ERR_ARG
 
 
+def test_empty_batch(ctx):
+    """k = 0 is a valid batch: nothing is launched and the call succeeds."""
+    for algo in (ot.OT_KM, ot.OT_BKM, ot.OT_AUTO):
+        a = ot.ot_assign_solve_batched(ctx, [], algo)
+        assert a.k == 0
+
+
 def _batch(k, lo, hi, seed):
     sizes = W.batch_sizes(k, lo, hi, seed)
     return [W.embedding_costs(int(n), seed=seed + 1 + i) for i, n in enumerate(sizes)]

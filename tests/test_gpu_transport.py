@@ -87,3 +87,23 @@ def test_transport_km_flow_matches_oracle(ctx, oracle_mod):
             assert cost == c0 and int((X * C).sum()) == c0
             np.testing.assert_array_equal(X.sum(1), r)
             assert (X.sum(0) <= c).all()
+
+
+def test_transport_degenerate_and_limits(ctx, oracle_mod):
+    """No supply (zero flow, zero cost, host or device C); one unit; the
+    argument checks (supply above demand, negative entries) and the size
+    limit of replication, all reported as error codes."""
+    C = np.arange(12, dtype=np.int32).reshape(3, 4)
+    for dev in (True, False):
+        Ct = torch.from_numpy(C).cuda() if dev else torch.from_numpy(C)
+        flow, cost = ot.ot_transport_solve(ctx, Ct, [0, 0, 0], [1, 0, 2, 0])
+        assert cost == 0 and not flow.cpu().numpy().any()
+    flow, cost = ot.ot_transport_solve(ctx, torch.from_numpy(C).cuda(), [0, 1, 0], [0, 0, 3, 1], ot.OT_KM)
+    f0, c0 = oracle_mod.transport(C, [0, 1, 0], [0, 0, 3, 1])
+    assert cost == c0 == 6 and np.array_equal(flow.cpu().numpy(), f0)
+    for sup, dem, code in [([2, 2, 2], [1, 1, 1, 1], ot.OT_ERR_ARG), ([1, -1, 1], [1, 1, 1, 1], ot.OT_ERR_ARG),
+                           ([1, 0, 0], [1, -2, 1, 1], ot.OT_ERR_ARG),
+                           ([1, 0, 0], [70000, 0, 0, 0], ot.OT_ERR_UNSUPPORTED)]:
+        with pytest.raises(ot.OtError) as e:
+            ot.ot_transport_solve(ctx, torch.from_numpy(C).cuda(), sup, dem)
+        assert e.value.code == code
