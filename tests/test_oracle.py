@@ -302,7 +302,7 @@ def _check_flow(C, r, c, flow, cost):
     assert int((flow * C.astype(np.int64)).sum()) == cost
 
 
-def test_transport_by_replication(oracle_mod):
+def _pin_transport_lp(transport):
     """Vertex replication turns integer-supply transport (Eq. 1) into an
     assignment problem with the same optimum: the folded flow is feasible,
     costs what the oracle reports, and that cost equals an LP optimum."""
@@ -314,7 +314,7 @@ def test_transport_by_replication(oracle_mod):
         if r.sum() > c.sum():
             c[0] += r.sum() - c.sum()
         C = rng.integers(-20, 100, size=(n, m)).astype(np.int32)
-        flow, cost = oracle_mod.transport(C, r, c)
+        flow, cost = transport(C, r, c)
         _check_flow(C, r, c, flow, cost)
         if r.sum() > 0:
             assert cost == _transport_lp(C, r, c)
@@ -322,7 +322,7 @@ def test_transport_by_replication(oracle_mod):
             assert cost == 0 and not flow.any()
 
 
-def test_transport_closed_forms(oracle_mod):
+def _pin_transport_closed_forms(transport, brute_force):
     """One source fills the cheapest columns first (a greedy optimum); one
     sink takes every unit; unit supplies and demands give the assignment."""
     rng = np.random.default_rng(37)
@@ -336,19 +336,56 @@ def test_transport_closed_forms(oracle_mod):
             take = min(left, int(c[j]))
             best += take * int(C[0, j])
             left -= take
-        flow, cost = oracle_mod.transport(C, [s], c)
+        flow, cost = transport(C, [s], c)
         _check_flow(C, [s], c, flow, cost)
         assert cost == best
         n = int(rng.integers(1, 6))
         C1 = rng.integers(-30, 30, size=(n, 1)).astype(np.int32)
         r1 = rng.integers(0, 4, n)
-        flow, cost = oracle_mod.transport(C1, r1, [int(r1.sum()) + int(rng.integers(0, 3))])
+        d1 = [int(r1.sum()) + int(rng.integers(0, 3))]
+        flow, cost = transport(C1, r1, d1)
+        _check_flow(C1, r1, d1, flow, cost)
         assert cost == int((C1[:, 0].astype(np.int64) * r1).sum())
         k = int(rng.integers(1, 7))
         Ck = rng.integers(0, 100, size=(k, k + 1)).astype(np.int32)
-        flow, cost = oracle_mod.transport(Ck, np.ones(k, int), np.ones(k + 1, int))
-        assert cost == oracle_mod.brute_force(Ck)[1]
-        assert (flow.sum(0) <= 1).all()
+        flow, cost = transport(Ck, np.ones(k, int), np.ones(k + 1, int))
+        _check_flow(Ck, np.ones(k, int), np.ones(k + 1, int), flow, cost)
+        assert cost == brute_force(Ck)[1]
+
+
+def test_transport_by_replication(oracle_mod):
+    _pin_transport_lp(oracle_mod.transport)
+
+
+def test_transport_closed_forms(oracle_mod):
+    _pin_transport_closed_forms(oracle_mod.transport, oracle_mod.brute_force)
+
+
+TRANSPORT_MUTANTS = [
+    ("np.add.at(flow, (rows, cols[a]), 1)", "np.add.at(flow, (rows, a % m), 1)"),  # column copies not folded
+    ("rows = np.repeat(np.arange(n), r)", "rows = np.repeat(np.arange(n), np.minimum(r, 1))"),  # supply dropped
+    ("cols = np.repeat(np.arange(m), c)", "cols = np.repeat(np.arange(m), c + 1)"),  # demand ignored
+    ("km(C[np.ix_(rows, cols)])", "km(-C[np.ix_(rows, cols)])"),  # wrong sign
+    ("return flow, int(cost)", "return flow, int(cost) - int(len(rows) > 1)"),  # cost off the flow's
+]
+
+
+@pytest.mark.parametrize("idx", range(len(TRANSPORT_MUTANTS)))
+def test_transport_pins_catch_planted_mistakes(oracle_mod, idx):
+    import inspect
+    src = inspect.getsource(oracle_mod.transport)
+    old, new = TRANSPORT_MUTANTS[idx]
+    assert old in src, old
+    ns = dict(vars(oracle_mod))
+    exec(src.replace(old, new, 1), ns)
+    caught = False
+    for pin in (lambda t: _pin_transport_lp(t), lambda t: _pin_transport_closed_forms(t, oracle_mod.brute_force)):
+        try:
+            pin(ns["transport"])
+        except (AssertionError, ValueError, IndexError):
+            caught = True
+            break
+    assert caught, f"transport mutant {idx} survived the pins"
 
 
 def test_stored_oracle_costs_reproduce(oracle_mod):
