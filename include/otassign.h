@@ -125,7 +125,7 @@ int ot_assign_solve_stats(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n,
 
 /* Batched KM with a single scaling factor s >= 1, the paper's approximate
  * variant (Sec. 2.3 "Batched KM": costs rounded to small integers by one
- * factor; Table 4 runs it as a 1.1-approximation).  The assignment problem
+ * factor; Table 3 runs it as a 1.1-approximation).  The assignment problem
  * is solved exactly on the scaled costs floor(C[i][j] / s) and the result's
  * cost under the original C is returned in *cost.  Writing
  * c = s*floor(c/s) + r with 0 <= r <= s-1 gives
