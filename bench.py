@@ -44,12 +44,25 @@ KERNEL_SOURCES = ["ot_group.cuh", "ot_group_km.cu", "ot_group_bkm.cu", "ot_group
                   "ot_internal.h", "ot_pack.cu"]
 
 
-def kernel_source_hash() -> str:
-    """sha256 over the sources that define the group-engine kernels."""
+def code_text(src: str) -> str:
+    """C/CUDA source with comments removed and whitespace collapsed: what the
+    compiler sees (comment edits do not count as kernel changes)."""
+    import re
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
+def kernel_source_hash(read=None) -> str:
+    """sha256 over the code (comments stripped) of the sources that define
+    the group-engine kernels; `read(name)` returns a source's text."""
     import hashlib
+    if read is None:
+        def read(f):
+            return open(os.path.join(ROOT, "paper_2005_01182_gb300", "csrc", f)).read()
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2005_01182_gb300", "csrc", f), "rb").read())
+        h.update(code_text(read(f)).encode())
     return h.hexdigest()
 
 
@@ -340,7 +353,7 @@ def measure_single_16384(ctx, stream, ot, torch):
 
 def measure_sinkhorn_4096(stream, ot, torch):
     """The paper's Sinkhorn protocol (Sec. 4.1) on the n = 4096 circle/square
-    instance: epsilon = 0.1% of the total demand, no rounding, and the
+    instance: epsilon = 10^-3 x the summed demand, no rounding, and the
     smallest eta of a geometric grid whose cost is within 110% of the exact
     optimum (batched KM here).  Time to convergence per eta."""
     ctx = ot.Context()

@@ -15,7 +15,7 @@
  *   OT_BKM  batched KM (Sec. 2.3 "Batched KM"): augmenting paths are routed
  *           in batches along tight edges from all free rows at once and the
  *           duals are adjusted across the cut between reached and unreached
- *           vertices in the same manner as KM.  Exact mode (scaling factor 1):
+ *           vertices, as KM adjusts them.  Exact mode (scaling factor 1):
  *           its optimal cost equals OT_KM's; assignment and duals may differ
  *           among optimal ones but always form a valid certificate.
  *

@@ -15,7 +15,7 @@ What each function follows in the paper:
   * ``bkm``          -- batched KM, exact mode (Sec. 2.3 "Batched KM").
   * ``check_certificate`` -- LP duality for Eq. 1 (weak duality makes a
     feasible dual with equal objective a proof of optimality).
-  * ``transport``    -- integer-supply transport (Eq. 1, Sec. 2) by vertex
+  * ``transport``    -- integer-supply transport (Eq. 1, Sec. 1) by vertex
     replication onto ``km``.
   * ``auction``      -- the auction algorithm with epsilon-scaling in
     parallel (Jacobi) rounds (Sec. 2.3.3 "The auction algorithm", Sec. 4.1
@@ -161,7 +161,7 @@ def auction(C, stats: bool = False):
 
 def transport(C, supply, demand):
     """Integer-supply transport (Eq. 1 with integer r and c, the
-    Hitchcock-Koopmans case of Sec. 2) by vertex replication: row i is
+    Hitchcock-Koopmans case of Sec. 1) by vertex replication: row i is
     repeated supply[i] times and column j demand[j] times, in index order,
     ``km`` solves the replicated assignment problem, and the flow counts the
     copies of row i matched to copies of column j.  Demands are capacities:

@@ -14,8 +14,8 @@ What it follows in the paper:
   * Sec. 2.2 "Matrix Scaling": the logarithms of the scalings are tracked
     instead of the scalings (the log domain), against under- and overflow.
     Here X_ij = exp(f_i + g_j - eta C_ij).
-  * Sec. 4.1 "Sinkhorn": epsilon is 0.1% of the total demand and the flow
-    is not rounded; the reported cost is <C, X> of the unrounded X.
+  * Sec. 4.1 "Sinkhorn": the stopping threshold is 10^-3 times the summed
+    demand, and the flow is not rounded; the reported cost is <C, X> of the unrounded X.
 
 Readings where the paper is silent:
   * start from f = g = 0; one iteration scales the rows (f) and then the

@@ -14,8 +14,8 @@
 // rows that just joined the tree (batched KM), only where j is outside T.
 //
 // Lazy duals.  Instead of touching every u_i, v_j and slack_j at every
-// dual adjustment (Sec. 2.3: "adjusts the dual potentials across a cut ...
-// in the same manner as KM"), a phase keeps distances relative to the duals
+// dual adjustment (Sec. 2.3: batched KM moves the duals across the cut of
+// reached vertices as KM does), a phase keeps distances relative to the duals
 // it started with and applies the accumulated adjustment once, when an
 // augmenting path is found: a column that entered T at distance dist_j gets
 // v_j -= D - dist_j and its matched row u += D - dist_j; every root gets

@@ -1,5 +1,5 @@
 // Optimal transport with integer supplies and demands (Eq. 1 with integer r
-// and c, the Hitchcock-Koopmans case of Sec. 2) by vertex replication: row i
+// and c, the Hitchcock-Koopmans case of Sec. 1) by vertex replication: row i
 // appears supply[i] times and column j demand[j] times, in index order, in an
 // assignment problem, whose matching is folded back into a flow matrix.
 #include <cstring>
