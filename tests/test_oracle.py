@@ -176,6 +176,19 @@ def test_km_stats_bytes(oracle_mod):
     assert st["steps"] == n and st["bytes"] == 4 * n * n and st["augmentations"] == n
 
 
+def test_km_counters_closed_form_all_ties(oracle_mod):
+    """All costs equal: in the phase of row r every slack is 0, so the lowest
+    column wins each step (0, 1, ..., r) and only column r is free; the
+    strict < keeps every predecessor at the root, so row r takes column r.
+    Phase r has r + 1 steps scanning m, m - 1, ..., m - r columns."""
+    for n, m in [(6, 6), (5, 9), (30, 30)]:
+        a, c, u, v, st = oracle_mod.km(np.zeros((n, m), np.int32), stats=True)
+        assert a.tolist() == list(range(n)) and c == 0
+        assert not u.any() and not v.any()
+        assert st["steps"] == n * (n + 1) // 2
+        assert st["bytes"] == 4 * sum((r + 1) * m - r * (r + 1) // 2 for r in range(n))
+
+
 def test_certificate_rejects_planted_errors(oracle_mod):
     from paper_2005_01182_gb300 import workloads as W
     C = W.pixel_sqdist(40, 45, seed=3)
@@ -201,6 +214,10 @@ MUTANTS = [
     ("km", "int64_t rc = AT(C, ldc, i, j) - u[i] - v[j];\n        bytes += 4;",
      "int64_t rc = AT(C, ldc, j % n, i) - u[i] - v[j];\n        bytes += 4;"),  # transposed operand
     ("km", "else slack[j] -= delta;", "else slack[j] -= 0;"),            # dropped term
+    ("km", "if (rc < slack[j]) { slack[j] = rc; pred[j] = i; }",
+     "if (rc <= slack[j]) { slack[j] = rc; pred[j] = i; }"),              # tie-break: latest predecessor
+    ("km", "if (!in_tree[j] && slack[j] < delta) { delta = slack[j]; jstar = j; }",
+     "if (!in_tree[j] && slack[j] <= delta) { delta = slack[j]; jstar = j; }"),  # tie-break: highest column
     ("bkm", "if (rc < delta) delta = rc;", "if (rc < delta) delta = rc + 1;"),   # off-by-one step
     ("bkm", "for (int j = 0; j < m; ++j) { int64_t c = AT(C, ldc, i, j); if (c < mn) mn = c; }",
      "for (int j = 1; j < m; ++j) { int64_t c = AT(C, ldc, i, j); if (c < mn) mn = c; }"),  # wrong index
@@ -226,6 +243,16 @@ def _mutant_check(so, fn_name, seed):
         cost = fn(P(C), ctypes.c_int64(m), n, m, P(a), P(u), P(v), P(st))
         if cost != py_brute(C) or oracle.check_certificate(C, a, u, v, cost) != 0:
             sys.exit(3)
+    if fn_name == "oracle_km":
+        # the tie-break rules, through the all-ties closed form
+        # (test_km_counters_closed_form_all_ties)
+        for n, m in [(6, 6), (5, 9)]:
+            C = np.zeros((n, m), np.int32)
+            a = np.zeros(n, np.int32); u = np.zeros(n, np.int64); v = np.zeros(m, np.int64)
+            st = np.zeros(4, np.int64)
+            fn(P(C), ctypes.c_int64(m), n, m, P(a), P(u), P(v), P(st))
+            if a.tolist() != list(range(n)) or st[0] != n * (n + 1) // 2:
+                sys.exit(4)
     sys.exit(0)
 
 
