@@ -96,13 +96,27 @@ typedef struct ot_stats {
                              16 bits, else equal to cost_bytes) */
 } ot_stats;
 
+/* Context configuration.  A zero-filled struct (with device = -1) gives the
+ * defaults; cfg = NULL in ot_ctx_create does the same. */
 typedef struct ot_config {
   int32_t device;            /* CUDA device ordinal; -1 = current device */
   int64_t hbm_budget_bytes;  /* serving arena = admission budget; 0 = 4 GiB */
   int32_t max_inflight;      /* serving: max requests resident at once; 0 = 4096 */
   int32_t wave_streams;      /* serving: streams used for overlapping waves; 0 = 4 */
   const char* tune_file;     /* autotuner table (JSON-lines); NULL = built-in */
+  uint32_t flags;            /* OT_CFG_* bits; 0 = defaults */
+  int32_t max_group_ctas;    /* upper bound on the CTAs of one batched group-engine
+                                launch; 0 = as many as fit on the device at once */
+  int64_t step_limit;        /* dependent tree-growing steps one instance may take in
+                                the warp/CTA group engine before its status becomes
+                                OT_ERR_TIMEOUT (its results are then undefined; the
+                                other instances are unaffected); 0 = only the built-in
+                                guards.  For failure-detection tests. */
 } ot_config;
+
+/* ot_config.flags */
+#define OT_CFG_NO_ROW_PACKING 1u  /* batched launches keep 32-bit cost rows (no 16-bit
+                                     packing pass, 64-bit solver arithmetic) */
 
 typedef struct ot_ctx ot_ctx;
 
@@ -244,6 +258,14 @@ int ot_assign_submit(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int3
 int ot_assign_poll(ot_ctx* ctx, uint64_t ticket, int32_t* row_to_col, int64_t* cost,
                    int64_t* u, int64_t* v);
 
+/* Cancel a submitted request: its result is discarded and its ticket
+ * retired (a later poll or cancel returns OT_ERR_TICKET).  A request still
+ * waiting for admission, or admitted but not yet launched, is dropped at
+ * once; a running one keeps its arena block until its solver has finished
+ * (the GPU work is not interrupted), then the block is returned to the
+ * budget.  OT_ERR_TICKET for an unknown, collected or cancelled ticket. */
+int ot_assign_cancel(ot_ctx* ctx, uint64_t ticket);
+
 /* Wait until every submitted request has finished (not collected). */
 int ot_assign_drain(ot_ctx* ctx);
 
@@ -291,17 +313,22 @@ int ot_tune_set(ot_ctx* ctx, int32_t algo, int32_t m, int32_t threads_per_instan
  * by every GPU that loads the library until the process exits.  Hence:
  *   - at most OT_NOALLOC_MAX_INSTANCES instances per call (else
  *     OT_ERR_UNSUPPORTED), each with m <= 4096 (else OT_ERR_UNSUPPORTED);
- *   - every pointer (element pointers, cost[k], status[k] when given) must be
- *     device memory on the current device (else OT_ERR_ARG): host data would
- *     need staging memory;
+ *   - every pointer (C[t], row_to_col[t], u[t] and v[t] when given, cost[k],
+ *     status[k] when given) must be device memory of the current device
+ *     (else OT_ERR_ARG, before anything is launched): host data would need
+ *     staging memory;
  *   - all calls share the array, so calls whose work overlaps on the GPU
  *     (different streams or threads) race: serialise them;
  *   - the first call on a device looks up the array's device address and may
- *     load the module; make that first call before any stream capture.
- * OT_AUTO resolves with the built-in table.  Results are identical to
- * ot_assign_solve_batched's with a context that has the built-in table.  Asynchronous on
- * `stream` (NULL = the legacy default stream); per-instance device status
- * codes go to status[k] when it is non-NULL. */
+ *     load the module; make that first call before any stream capture;
+ *   - the metadata is uploaded from host bookkeeping that the next call
+ *     overwrites, so a call on a stream that is being captured returns
+ *     OT_ERR_UNSUPPORTED.
+ * An instance with n == 0 gets cost 0, status 0 and (when v[t] is given)
+ * v = 0.  OT_AUTO resolves with the built-in table.  Results are identical to
+ * ot_assign_solve_batched's with a context that has the built-in table.
+ * Asynchronous on `stream` (NULL = the legacy default stream); per-instance
+ * device status codes go to status[k] when it is non-NULL. */
 #define OT_NOALLOC_MAX_INSTANCES 1024
 int ot_assign_solve_batched_noalloc(int32_t k, const int32_t* const* C, const int64_t* ldc,
                                     const int32_t* n, const int32_t* m, int32_t algo,

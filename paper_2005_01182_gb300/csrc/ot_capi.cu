@@ -213,17 +213,6 @@ static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 // cached CUDA graph)
 // ---------------------------------------------------------------------------
 
-// OT_GROUP_MAX_CTAS caps the persistent grid of batched launches
-// (experiments on how many instances should be in flight at once).
-static int max_ctas_env() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = std::getenv("OT_GROUP_MAX_CTAS");
-    v = e ? std::max(0, std::atoi(e)) : 0;
-  }
-  return v;
-}
-
 struct Bucket {
   int shape;
   int algo = 0;
@@ -231,21 +220,13 @@ struct Bucket {
   std::vector<int> idx;
 };
 
-// 16-bit row packing for group-engine instances (OT_PACK=0 disables it).
-static bool packing_enabled() {
-  static const bool on = [] {
-    const char* e = std::getenv("OT_PACK");
-    return !(e && std::atoi(e) == 0);
-  }();
-  return on;
-}
-
 // insts[t] already holds device pointers; entries with skip[t] set are not
 // launched.  Writes per-instance stats into ctx->d_stats (k x 8).
 int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts,
                      const std::vector<int>& skip, int algo, cudaStream_t stream, bool fork,
                      bool own_stats, std::vector<int>* unsupported, bool allow_cluster) {
   const int k = int(insts.size());
+  for (Instance& I : insts) I.step_limit = ctx->step_limit;
   if (own_stats) {
     if (int rc = slot.d_stats.reserve(size_t(k) * 8 * sizeof(int64_t)); rc) return ctx_fail(ctx, rc, "stats alloc");
     int64_t* dstats = static_cast<int64_t*>(slot.d_stats.ptr);
@@ -303,7 +284,7 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
     b.mmax = std::max(b.mmax, I.m);
     b.idx.push_back(t);
   }
-  const bool pack_on = packing_enabled();
+  const bool pack_on = ctx->pack_rows;
   bool any_pack = false;
   if (pack_on && slot.pack && !buckets.empty()) {
     size_t nrows = 0, nelem = 0;
@@ -424,7 +405,7 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
       e = launch_auction(b.shape, dinst, dorder + offs[bi], int(b.idx.size()), dwork + bi, b.mmax, s);
     else
       e = launch_group(group_shape(b.shape), b.algo, dinst, dorder + offs[bi], int(b.idx.size()), dwork + bi,
-                       b.nmax, b.mmax, max_ctas_env(), s);
+                       b.nmax, b.mmax, ctx->max_group_ctas, s);
     if (e == cudaSuccess && timed) e = cudaEventRecordWithFlags(slot.tev[2 * bi + 1], s, cudaEventRecordExternal);
     return e;
   };
@@ -566,6 +547,7 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
     for (int t = 0; t < k; ++t) {
       if (n[t] == 0 && st[t] == OT_OK) {
         if ((e = cudaMemsetAsync(cost + t, 0, sizeof(int64_t), stream)) != cudaSuccess) return ctx_cuda(ctx, e, "memset");
+        if ((e = cudaMemsetAsync(dstatus + t, 0, sizeof(int32_t), stream)) != cudaSuccess) return ctx_cuda(ctx, e, "memset");
         if (v && v[t] && m[t] > 0) cudaMemsetAsync(v[t], 0, sizeof(int64_t) * m[t], stream);
       }
     }
@@ -853,6 +835,9 @@ int ot_ctx_create(ot_ctx** out, const ot_config* cfg) {
     ctx->tune_file = c.tune_file;
     load_tune_file(ctx);
   }
+  ctx->pack_rows = (c.flags & OT_CFG_NO_ROW_PACKING) == 0;
+  ctx->max_group_ctas = std::max(0, c.max_group_ctas);
+  ctx->step_limit = std::max<int64_t>(0, c.step_limit);
   if (int rc = serve_init(ctx, c); rc) { ot_ctx_destroy(ctx); return rc; }
   if (cudaGetLastError() != cudaSuccess) { ot_ctx_destroy(ctx); return OT_ERR_CUDA; }
   *out = ctx;
@@ -1086,7 +1071,7 @@ int ot_autotune(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* 
   // time what the solves run: rows packed to 16 bits (and the 32-bit path)
   // whenever the batched launches pack them
   bool packed = false;
-  if (packing_enabled()) {
+  if (ctx->pack_rows) {
     size_t nrows = 0, nelem = 0;
     for (auto& kv : byb)
       for (int t : kv.second) { nrows += size_t(n[t]); nelem += size_t(n[t]) * m[t]; }

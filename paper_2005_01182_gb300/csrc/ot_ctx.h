@@ -109,6 +109,9 @@ struct ot_ctx {
   bool tuned[2][ot::kNumBuckets] = {};  // entry set by ot_tune_set / ot_autotune / tune file
   int auto_algo[ot::kNumBuckets];  // algorithm OT_AUTO resolves to, per bucket
   std::string tune_file;
+  bool pack_rows = true;        // 16-bit row packing of group-engine instances
+  int max_group_ctas = 0;       // cap on a batched launch's persistent grid (0: none)
+  long long step_limit = 0;     // per-instance step cap (failure-detection tests)
 
   int last_k = 0;               // instances of the most recent API call
   std::vector<int> last_skip;   // which of them were not launched

@@ -255,7 +255,12 @@ __device__ __forceinline__ void solve_instance_v(const Instance& I, const GroupS
 
     int guard = 0;
     for (;;) {
-      if (++guard > m + 2) { status = kDevStepLimit; break; }
+      // bounded: at most m + 2 steps per phase, and the caller's step cap
+      if (++guard > m + 2 ||
+          (I.step_limit > 0 && (ALGO == kAlgoKM ? steps + guard : steps + 1) > I.step_limit)) {
+        status = kDevStepLimit;
+        break;
+      }
       if constexpr (ALGO == kAlgoBKM) {
         if (t == 0) S.misc[p ^ 1] = 0;
       }

@@ -28,6 +28,9 @@ struct Instance {
   const uint16_t* P;
   const int32_t* roff;
   const int32_t* pok;
+  // Dependent steps the instance may take before its status becomes the
+  // step-limit code (0: only the built-in guards apply).
+  long long step_limit;
 };
 
 // Pack the rows of `num` instances (insts[order[t]], P/roff/pok set) into

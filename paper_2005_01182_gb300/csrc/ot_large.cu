@@ -1021,9 +1021,7 @@ static int large_cluster_size() {
   static int cached = 0;
   if (cached) return cached;
   // 16 CTAs when the device allows it (n = 16384 batched KM: 1.37 s vs
-  // 1.66 s with 8); OT_LARGE_CLUSTER=8 forces the portable size
-  const char* env = std::getenv("OT_LARGE_CLUSTER");
-  if (env && std::atoi(env) == 8) return cached = 8;
+  // 1.66 s with 8)
   int best = 8;
   auto kern = large_steps<1, kAlgoBKM>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
@@ -1094,7 +1092,7 @@ int solve_large(ot_ctx* ctx, const Instance& I, int algo, cudaStream_t stream, i
   w.ctl = reinterpret_cast<LargeCtl*>(B + o_ctl);
   w.chunks = chunks;
   w.vec4 = (I.ldc % 4 == 0) && (reinterpret_cast<uintptr_t>(I.C) % 16 == 0);
-  w.tma = w.vec4 && (m % 4 == 0) && !std::getenv("OT_LARGE_NO_TMA");
+  w.tma = w.vec4 && (m % 4 == 0);
 
   cudaError_t e = cudaMemsetAsync(I.cost, 0, sizeof(int64_t), stream);
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "large memset");
@@ -1107,7 +1105,7 @@ int solve_large(ot_ctx* ctx, const Instance& I, int algo, cudaStream_t stream, i
     const int ttiles = (m + kTmaTileCols - 1) / kTmaTileCols;
     const int tchunks = std::max(1, std::min((2 * sms + ttiles - 1) / ttiles, chunks));
     const dim3 tgrid(ttiles, tchunks, 1);
-    const bool pass_tma = w.tma && !std::getenv("OT_PASS_NO_TMA");
+    const bool pass_tma = w.tma;
     if (pass_tma) {
       w.chunks = tchunks;  // the step kernel reduces exactly the partials the pass writes
       if ((e = cudaFuncSetAttribute(large_pass_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaPassSmem)) !=

@@ -87,6 +87,8 @@ struct Req {
   size_t bytes = 0, off = 0;
   int flag = -1;                 // slot in the mapped status array
   bool admitted = false, launched = false;
+  bool submitting = true;        // submit() has not returned the ticket yet
+  bool cancelled = false;        // cancelled while its wave runs: reclaimed once finished
   std::vector<int32_t> host_C;  // packed copy while waiting for admission
 };
 
@@ -134,11 +136,14 @@ struct ServeState {
   cudaStream_t copy_stream = nullptr, poll_stream = nullptr;
   cudaEvent_t copy_ev = nullptr;
   int64_t n_submitted = 0, n_admitted = 0, n_completed = 0, n_waves = 0, max_busy = 0, n_refused = 0;
+  int n_cancel_wait = 0;  // cancelled requests whose wave has not finished
 
   int start();
   void loop();
   bool try_admit(uint64_t t, Req& r);
   void launch_ready();
+  void release(uint64_t t, Req& r);
+  void reclaim_cancelled();
 };
 
 int ServeState::start() {
@@ -184,6 +189,32 @@ bool ServeState::try_admit(uint64_t, Req& r) {
   ++inflight;
   ++n_admitted;
   return true;
+}
+
+// Caller holds mu.  Return request t's arena block and status slot and
+// forget it.
+void ServeState::release(uint64_t t, Req& r) {
+  if (r.admitted) {
+    arena.release(r.off, r.bytes);
+    free_flags.push_back(r.flag);
+    --inflight;
+  }
+  reqs.erase(t);
+}
+
+// Caller holds mu.  Cancelled requests whose solver has written its status
+// word no longer use their block.
+void ServeState::reclaim_cancelled() {
+  if (n_cancel_wait == 0) return;
+  std::vector<uint64_t> done;
+  for (auto& kv : reqs) {
+    const Req& r = kv.second;
+    if (r.cancelled && *reinterpret_cast<volatile int32_t*>(&flags[r.flag]) != kFlagPending) done.push_back(kv.first);
+  }
+  for (uint64_t t : done) {
+    release(t, reqs[t]);
+    --n_cancel_wait;
+  }
 }
 
 // Caller holds mu.  Launch every admitted request as one wave.
@@ -268,6 +299,7 @@ void ServeState::loop() {
       }
     }
     launch_ready();
+    reclaim_cancelled();
   }
 }
 
@@ -361,6 +393,7 @@ int ot_assign_submit(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int3
     s->reqs.erase(t);
     return ctx_cuda(ctx, e, "submit copy");
   }
+  rr.submitting = false;
   if (now) {
     s->ready.push_back(t);
   } else {
@@ -381,6 +414,7 @@ int ot_assign_poll(ot_ctx* ctx, uint64_t ticket, int32_t* row_to_col, int64_t* c
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return ctx_fail(ctx, OT_ERR_TICKET, "unknown ticket");
   Req& r = it->second;
+  if (r.cancelled || r.submitting) return ctx_fail(ctx, OT_ERR_TICKET, "unknown ticket");
   if (!r.launched) return OT_PENDING;
   const int32_t f = *reinterpret_cast<volatile int32_t*>(&s->flags[r.flag]);
   if (f == kFlagPending) return OT_PENDING;
@@ -411,6 +445,37 @@ int ot_assign_poll(ot_ctx* ctx, uint64_t ticket, int32_t* row_to_col, int64_t* c
   s->cv.notify_one();
   if (rc != OT_OK && rc != OT_ERR_CUDA) return ctx_fail(ctx, rc, "request failed on the device");
   return rc;
+}
+
+int ot_assign_cancel(ot_ctx* ctx, uint64_t ticket) {
+  if (!ctx) return OT_ERR_ARG;
+  ServeState* s = ctx->serve;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end() || it->second.cancelled || it->second.submitting)
+    return ctx_fail(ctx, OT_ERR_TICKET, "unknown ticket");
+  Req& r = it->second;
+  if (!r.admitted) {
+    // waiting for admission in the host queue (the queue skips it)
+    s->reqs.erase(it);
+    return OT_OK;
+  }
+  if (!r.launched) {
+    // admitted, its copy landed, not yet in a wave
+    s->ready.erase(std::remove(s->ready.begin(), s->ready.end(), ticket), s->ready.end());
+    s->release(ticket, r);
+    lk.unlock();
+    s->cv.notify_one();
+    return OT_OK;
+  }
+  // in a wave: its solver may still write into the block, which is returned
+  // once the status word shows the solve has ended; the result is discarded
+  r.cancelled = true;
+  ++s->n_cancel_wait;
+  s->reclaim_cancelled();
+  lk.unlock();
+  s->cv.notify_one();
+  return OT_OK;
 }
 
 int ot_assign_drain(ot_ctx* ctx) {

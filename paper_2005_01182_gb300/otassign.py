@@ -53,7 +53,11 @@ class ot_stats(ctypes.Structure):
 class ot_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
                 ("max_inflight", ctypes.c_int32), ("wave_streams", ctypes.c_int32),
-                ("tune_file", ctypes.c_char_p)]
+                ("tune_file", ctypes.c_char_p), ("flags", ctypes.c_uint32),
+                ("max_group_ctas", ctypes.c_int32), ("step_limit", ctypes.c_int64)]
+
+
+OT_CFG_NO_ROW_PACKING = 1
 
 
 def declared_symbols() -> list[str]:
@@ -87,6 +91,7 @@ def load(path: str | None = None):
         "ot_assign_submit": (ctypes.c_int, [vp, vp, i64, i32, i32, i32, ctypes.POINTER(ctypes.c_uint64)]),
         "ot_assign_poll": (ctypes.c_int, [vp, ctypes.c_uint64, vp, vp, vp, vp]),
         "ot_assign_drain": (ctypes.c_int, [vp]),
+        "ot_assign_cancel": (ctypes.c_int, [vp, ctypes.c_uint64]),
         "ot_serving_counters": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
         "ot_autotune": (ctypes.c_int, [vp, i32, pp, ctypes.POINTER(i64), ctypes.POINTER(i32),
                                        ctypes.POINTER(i32), i32, i32]),
@@ -141,10 +146,11 @@ class Context:
     """Owns one ot_ctx (device buffers, streams, serving thread)."""
 
     def __init__(self, device: int = -1, hbm_budget_bytes: int = 0, max_inflight: int = 0,
-                 wave_streams: int = 0, tune_file: str | None = None):
+                 wave_streams: int = 0, tune_file: str | None = None, flags: int = 0,
+                 max_group_ctas: int = 0, step_limit: int = 0):
         lib = load()
         cfg = ot_config(device, hbm_budget_bytes, max_inflight, wave_streams,
-                        tune_file.encode() if tune_file else None)
+                        tune_file.encode() if tune_file else None, flags, max_group_ctas, step_limit)
         h = ctypes.c_void_p()
         rc = lib.ot_ctx_create(ctypes.byref(h), ctypes.byref(cfg))
         if rc != OT_OK:
@@ -390,6 +396,12 @@ def ot_assign_poll(ctx: Context, ticket: int, out) -> int:
         return OT_PENDING
     ctx._raise(rc, "ot_assign_poll")
     return OT_OK
+
+
+def ot_assign_cancel(ctx: Context, ticket: int):
+    """Cancel a submitted request (raises OtError OT_ERR_TICKET for an
+    unknown, collected or already cancelled ticket)."""
+    ctx._raise(ctx.lib.ot_assign_cancel(ctx.h, ticket), "ot_assign_cancel")
 
 
 def ot_assign_drain(ctx: Context):

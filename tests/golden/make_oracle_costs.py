@@ -17,6 +17,7 @@ from paper_2005_01182_gb300 import workloads as W  # noqa: E402
 
 CASES = {
     "single_4096_circle_square": lambda: W.single_4096("circle-square"),
+    "single_4096_circle_triangle": lambda: W.single_4096("circle-triangle"),
     "single_4096_uniform": lambda: W.single_4096("uniform"),
     "single_16384_grid": W.single_16384,
 }

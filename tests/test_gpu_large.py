@@ -113,7 +113,7 @@ def test_single_16384(oracle_mod, ctx):
     assert stored is None or stored == c
 
 
-@pytest.mark.parametrize("kind", ["circle-square", "uniform"])
+@pytest.mark.parametrize("kind", ["circle-square", "circle-triangle", "uniform"])
 def test_single_4096_matches_stored_oracle_cost(ctx, kind):
     """n = 4096 single solves (both engines, KM and batched KM) against the
     oracle's stored optimum."""

@@ -426,5 +426,6 @@ def test_stored_oracle_costs_reproduce(oracle_mod):
         f = line.split()
         if f and not line.startswith("#"):
             stored[f[0]] = int(f[1])
-    assert set(stored) == {"single_4096_circle_square", "single_4096_uniform", "single_16384_grid"}
+    assert set(stored) == {"single_4096_circle_square", "single_4096_circle_triangle", "single_4096_uniform",
+                           "single_16384_grid"}
     assert oracle_mod.km(W.single_4096("uniform"))[1] == stored["single_4096_uniform"]

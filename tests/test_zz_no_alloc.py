@@ -72,3 +72,36 @@ def test_noalloc_rejects_what_it_cannot_hold(lib_path):
     host = [torch.zeros((4, 4), dtype=torch.int32)]
     a = ot.BatchArgs(host, device="cpu")
     assert ot.ot_assign_solve_batched_noalloc(a) == ot.OT_ERR_ARG
+    # device costs, but one output array on the host: refused before any
+    # launch (the kernel would write through a host address)
+    dev = [torch.zeros((4, 4), dtype=torch.int32, device="cuda")]
+    for which in ("rp", "up", "vp"):
+        a = ot.BatchArgs(dev)
+        hosted = torch.empty(4, dtype=torch.int32 if which == "rp" else torch.int64)
+        getattr(a, which)[0] = hosted.data_ptr()
+        assert ot.ot_assign_solve_batched_noalloc(a) == ot.OT_ERR_ARG, which
+    torch.cuda.synchronize()
+
+
+def test_noalloc_empty_instance_in_a_mix(lib_path):
+    """n == 0 gives cost 0 and status 0, as the context path returns it."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    Cs = [torch.from_numpy(W.pixel_sqdist(n, n + 3, seed=n)).cuda() for n in (5, 40)]
+    Cs.insert(1, torch.zeros((0, 6), dtype=torch.int32, device="cuda"))
+    a = ot.BatchArgs(Cs)
+    a.cost.fill_(-7)
+    a.status.fill_(-7)
+    a.outs[1][2].fill_(-7)
+    assert ot.ot_assign_solve_batched_noalloc(a, ot.OT_KM) == ot.OT_OK
+    torch.cuda.synchronize()
+    ctx = ot.Context()
+    try:
+        ref = ot.ot_assign_solve_batched(ctx, Cs, ot.OT_KM)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(a.cost.cpu().numpy(), ref.cost.cpu().numpy())
+    finally:
+        ctx.close()
+    assert a.cost[1].item() == 0
+    assert (a.status.cpu().numpy() == 0).all()
+    assert (a.outs[1][2].cpu().numpy() == 0).all()
