@@ -117,6 +117,9 @@ typedef struct ot_config {
 /* ot_config.flags */
 #define OT_CFG_NO_ROW_PACKING 1u  /* batched launches keep 32-bit cost rows (no 16-bit
                                      packing pass, 64-bit solver arithmetic) */
+#define OT_CFG_DENSE_WIDE 2u      /* batched-KM instances too wide for one CTA run on the
+                                     dense cluster engine (every tree row scanned in full)
+                                     instead of the sparse-list engine; same results */
 
 typedef struct ot_ctx ot_ctx;
 

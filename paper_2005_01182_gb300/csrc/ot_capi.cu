@@ -473,6 +473,11 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<Instance>& insts
   return OT_OK;
 }
 
+int solve_wide(ot_ctx* ctx, const Instance& I, int algo, cudaStream_t stream, int64_t* stats_out) {
+  if (algo == kAlgoBKM && !ctx->dense_wide && I.m <= sparse_max_cols()) return solve_sparse(ctx, I, stream, stats_out);
+  return solve_large(ctx, I, algo, stream, stats_out);
+}
+
 // Validate one instance's sizes.
 static int check_sizes(const void* C, int64_t ldc, int n, int m) {
   if (n < 0 || m < 0 || n > m) return OT_ERR_ARG;
@@ -539,7 +544,7 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
         ctx->last_skip[t] = 1;
         continue;
       }
-      const int rc = solve_large(ctx, insts[t], resolve_algo(ctx, algo, insts[t].m), stream, nullptr);
+      const int rc = solve_wide(ctx, insts[t], resolve_algo(ctx, algo, insts[t].m), stream, nullptr);
       if (rc == OT_ERR_TIMEOUT || rc == OT_ERR_UNSUPPORTED) { st[t] = rc; continue; }
       if (rc != OT_OK) return rc;
     }
@@ -694,7 +699,7 @@ static int solve_many(ot_ctx* ctx, int k, const int32_t* const* C, const int64_t
   std::vector<int> still;
   for (int t : unsup) {
     if (insts[t].m > large_max_cols() || algo == OT_AUCTION) { still.push_back(t); continue; }
-    const int rc = solve_large(ctx, insts[t], resolve_algo(ctx, algo, insts[t].m), stream, nullptr);
+    const int rc = solve_wide(ctx, insts[t], resolve_algo(ctx, algo, insts[t].m), stream, nullptr);
     if (rc == OT_ERR_TIMEOUT || rc == OT_ERR_UNSUPPORTED) { st[t] = rc; skip[t] = 1; continue; }
     if (rc != OT_OK) return rc;
   }
@@ -838,6 +843,7 @@ int ot_ctx_create(ot_ctx** out, const ot_config* cfg) {
   ctx->pack_rows = (c.flags & OT_CFG_NO_ROW_PACKING) == 0;
   ctx->max_group_ctas = std::max(0, c.max_group_ctas);
   ctx->step_limit = std::max<int64_t>(0, c.step_limit);
+  ctx->dense_wide = (c.flags & OT_CFG_DENSE_WIDE) != 0;
   if (int rc = serve_init(ctx, c); rc) { ot_ctx_destroy(ctx); return rc; }
   if (cudaGetLastError() != cudaSuccess) { ot_ctx_destroy(ctx); return OT_ERR_CUDA; }
   *out = ctx;

@@ -112,6 +112,7 @@ struct ot_ctx {
   bool pack_rows = true;        // 16-bit row packing of group-engine instances
   int max_group_ctas = 0;       // cap on a batched launch's persistent grid (0: none)
   long long step_limit = 0;     // per-instance step cap (failure-detection tests)
+  bool dense_wide = false;      // wide batched-KM instances on the dense cluster engine
 
   int last_k = 0;               // instances of the most recent API call
   std::vector<int> last_skip;   // which of them were not launched
@@ -167,6 +168,14 @@ int run_device_batch(ot_ctx* ctx, LaunchSlot& slot, std::vector<ot::Instance>& i
 // cluster plus grid-wide passes; synchronises `stream`.
 int solve_large(ot_ctx* ctx, const ot::Instance& I, int algo, cudaStream_t stream, int64_t* stats_out);
 int large_max_cols();
+// Sparse-list engine (ot_sparse.cu): one batched-KM instance with
+// n <= m <= sparse_max_cols(); synchronises `stream`.
+int solve_sparse(ot_ctx* ctx, const ot::Instance& I, cudaStream_t stream, int64_t* stats_out);
+int sparse_max_cols();
+// An instance the group engine does not take: batched KM on the sparse-list
+// engine when it fits (unless the context asks for the dense cluster
+// engine), everything else on the cluster engine.
+int solve_wide(ot_ctx* ctx, const ot::Instance& I, int algo, cudaStream_t stream, int64_t* stats_out);
 // OT_KM / OT_BKM unchanged; OT_AUTO -> the tuned algorithm of m's bucket.
 int resolve_algo(const ot_ctx* ctx, int algo, int m);
 int serve_init(ot_ctx* ctx, const ot_config& cfg);

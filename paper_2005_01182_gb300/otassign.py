@@ -58,6 +58,7 @@ class ot_config(ctypes.Structure):
 
 
 OT_CFG_NO_ROW_PACKING = 1
+OT_CFG_DENSE_WIDE = 2
 
 
 def declared_symbols() -> list[str]:
