@@ -1114,7 +1114,7 @@ int solve_large(ot_ctx* ctx, const Instance& I, int algo, cudaStream_t stream, i
     }
     int batch = 4;
     LargeCtl h;
-    for (int iter = 0; iter < 4 * n + 8; iter += batch) {
+    for (long long launched = 0; launched < 4ll * n + 8;) {
       for (int b = 0; b < batch; ++b) {
         if (pass_tma) {
           large_pass_tma<<<tgrid, kPassThreads, kTmaPassSmem, stream>>>(w);
@@ -1128,8 +1128,9 @@ int solve_large(ot_ctx* ctx, const Instance& I, int algo, cudaStream_t stream, i
       if ((e = cudaMemcpyAsync(&h, w.ctl, sizeof(h), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
         return ctx_cuda(ctx, e, "large ctl");
       if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return ctx_cuda(ctx, e, "large sync");
+      launched += batch;
       if (h.done) break;
-      batch = std::min(batch * 2, 64);
+      if (batch < 64) batch *= 2;
     }
   }
   large_final<<<sms, 256, 0, stream>>>(w, I);
