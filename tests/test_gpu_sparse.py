@@ -26,6 +26,17 @@ def dense_ctx(lib_path):
     c.close()
 
 
+@pytest.fixture(scope="module")
+def sparse_ctx(lib_path):
+    """A context of its own: an untuned table routes single batched-KM
+    solves wider than 1024 columns to the wide engines."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = ot.Context()
+    yield c
+    c.close()
+
+
 def solve(ctx, C, algo=ot.OT_BKM):
     r, c, u, v, st = ot.ot_assign_solve_stats(ctx, torch.from_numpy(np.ascontiguousarray(C)).cuda(), algo)
     return r.cpu().numpy(), int(c.item()), u.cpu().numpy(), v.cpu().numpy(), st
@@ -52,9 +63,9 @@ def make(kind, n, m, seed):
 
 
 @pytest.mark.parametrize("kind,n,m", CASES)
-def test_sparse_equals_dense_engine(oracle_mod, ctx, dense_ctx, kind, n, m):
+def test_sparse_equals_dense_engine(oracle_mod, sparse_ctx, dense_ctx, kind, n, m):
     C = make(kind, n, m, seed=n + m)
-    a, c, u, v, st = solve(ctx, C)
+    a, c, u, v, st = solve(sparse_ctx, C)
     a2, c2, u2, v2, st2 = solve(dense_ctx, C)
     assert c == c2
     np.testing.assert_array_equal(a, a2)
@@ -67,21 +78,21 @@ def test_sparse_equals_dense_engine(oracle_mod, ctx, dense_ctx, kind, n, m):
     assert st["cost_bytes"] < st2["cost_bytes"]
 
 
-def test_sparse_small_and_degenerate(oracle_mod, ctx):
+def test_sparse_small_and_degenerate(oracle_mod, sparse_ctx):
     """Rows and columns of one, all-equal and all-zero costs, very few rows
     against many columns; optimum and certificate against the oracle."""
     cases = [np.zeros((1, 1), np.int32), np.array([[5, 3, 9]], np.int32),
              np.zeros((40, 1500), np.int32), np.full((1200, 1200), 7, np.int32),
              W.uniform_costs(3, 16384, seed=9), W.pixel_sqdist(1025, 1030, seed=3)]
     for C in cases:
-        a, c, u, v, _ = solve(ctx, C)
+        a, c, u, v, _ = solve(sparse_ctx, C)
         assert c == oracle_mod.km(C)[1]
         assert oracle_mod.check_certificate(C, a, u, v, c) == 0
 
 
-def test_sparse_width_limit_falls_back_to_cluster_engine(oracle_mod, ctx):
+def test_sparse_width_limit_falls_back_to_cluster_engine(oracle_mod, sparse_ctx):
     """Batched KM wider than 16384 columns stays on the cluster engine."""
     C = W.uniform_costs(5, 16390, seed=4)
-    a, c, u, v, _ = solve(ctx, C)
+    a, c, u, v, _ = solve(sparse_ctx, C)
     assert c == oracle_mod.km(C)[1]
     assert oracle_mod.check_certificate(C, a, u, v, c) == 0
