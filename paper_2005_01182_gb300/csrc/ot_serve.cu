@@ -3,13 +3,14 @@
 // submit() reserves a block of a device arena (the HBM budget) for the
 // request -- cost matrix, duals, assignment, counters -- and copies the cost
 // matrix in; a request that does not fit yet waits in a host-side queue with
-// its own copy of C.  A serving thread packs every admitted request into a
-// wave and launches it on one of several streams, so waves formed while
-// earlier ones still run overlap on the device.  Each request finishes on
-// its own: the solver group writes the results and then, after a
-// system-scope fence, a status word in mapped host memory, which poll()
-// reads without waiting for the rest of the wave.  poll() copies the
-// results out and frees the arena block, which lets queued requests in.
+// its own copy of C.  Requests with m <= 2048 are published, as soon as
+// their matrix is in the arena, to a persistent grid of solver groups that
+// pull them from a ring one by one (a request starts as soon as a group is
+// free, whatever else is running); wider ones are packed into waves launched
+// on several streams.  Each request finishes on its own: the solver group
+// writes the results and then, after a system-scope fence, a status word in
+// mapped host memory, which poll() reads.  poll() copies the results out and
+// frees the arena block, which lets queued requests in.
 #include <algorithm>
 
 #ifndef OT_SERVE_PACK
@@ -113,6 +114,85 @@ struct Layout {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Persistent serving grid.  Resident solver groups of kPTPI threads (each
+// owning kPK columns per thread, so m <= kPMaxCols) pull request
+// descriptors from a ring in mapped host memory as the serving thread
+// publishes them, solve each request (KM or batched KM, the group engine's
+// step sequence) and write its status word, then pull the next one.  Every
+// wait is bounded: a group that finds the ring empty polls with a growing
+// sleep and leaves after kIdlePolls polls (the host relaunches the grid when
+// new work arrives and none is resident); a stop flag ends it at once.
+// ---------------------------------------------------------------------------
+constexpr int kPTPI = 512, kPK = 4;
+constexpr int kPMaxCols = kPTPI * kPK;
+constexpr int kIdlePolls = 1 << 14;
+
+struct PQueue {                    // mapped pinned host memory
+  unsigned long long tail;         // requests published (written by the host)
+  int stop;                        // the host asks the grid to leave
+  int pad;
+};
+
+struct PItem {                     // one published request
+  Instance I;
+  int algo;
+  int pad;
+};
+static_assert(sizeof(PItem) % 8 == 0, "descriptor copied in 8-byte words");
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(kPTPI) serve_kernel(PQueue* q, const PItem* ring, int cap,
+                                                      unsigned long long* head) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int kWords = int(sizeof(PItem) / 8);
+  __shared__ long long s_slot;
+  __shared__ unsigned long long s_item[kWords];
+  const int t = threadIdx.x;
+  for (;;) {
+    if (t == 0) {
+      long long slot = -1;
+      for (int poll = 0; poll < kIdlePolls && slot < 0; ++poll) {
+        if (*reinterpret_cast<volatile int*>(&q->stop)) break;
+        const unsigned long long tl = ld_acquire_sys(&q->tail);
+        const unsigned long long h = *reinterpret_cast<volatile unsigned long long*>(head);
+        if (h < tl) {
+          if (atomicCAS(head, h, h + 1) == h) slot = (long long)h;
+        } else {
+          __nanosleep(poll < 32 ? 256 : 4096);
+        }
+      }
+      s_slot = slot;
+      if (slot >= 0) {
+        // the descriptor, read past any cached copy of an earlier use of
+        // the slot
+        const volatile unsigned long long* src =
+            reinterpret_cast<const volatile unsigned long long*>(ring + slot % cap);
+        for (int x = 0; x < kWords; ++x) s_item[x] = src[x];
+      }
+    }
+    __syncthreads();
+    const long long slot = s_slot;
+    if (slot < 0) break;
+    const PItem& it = *reinterpret_cast<const PItem*>(s_item);
+    const Instance I = it.I;
+    const int algo = it.algo;
+    __syncthreads();  // every thread has read s_slot and the descriptor
+    if (algo == kAlgoKM) {
+      const GroupSmem S = carve(smem_raw, kPTPI, kAlgoKM, kPMaxCols, kPMaxCols);
+      solve_instance<kPTPI, kPK, kAlgoKM>(I, S, t);
+    } else {
+      const GroupSmem S = carve(smem_raw, kPTPI, kAlgoBKM, kPMaxCols, kPMaxCols);
+      solve_instance<kPTPI, kPK, kAlgoBKM>(I, S, t);
+    }
+  }
+}
+
 }  // namespace
 
 struct ServeState {
@@ -138,9 +218,27 @@ struct ServeState {
   int64_t n_submitted = 0, n_admitted = 0, n_completed = 0, n_waves = 0, max_busy = 0, n_refused = 0;
   int n_cancel_wait = 0;  // cancelled requests whose wave has not finished
 
+  // persistent grid (requests with m <= kPMaxCols)
+  PQueue* pq = nullptr;                 // mapped pinned host memory
+  PQueue* dpq = nullptr;                // its device address
+  PItem* pring = nullptr;               // mapped ring of published requests
+  PItem* dpring = nullptr;
+  unsigned long long* dhead = nullptr;  // requests taken by the grid (device)
+  int pcap = 0;
+  unsigned long long ptail = 0;         // requests published
+  cudaStream_t pstream = nullptr;
+  cudaEvent_t pev = nullptr;            // end of the latest grid launch
+  bool prun = false;
+  int pgrid = 0;
+  size_t psmem = 0;
+  std::vector<uint64_t> plive;          // published, status not yet seen final
+
   int start();
   void loop();
   bool try_admit(uint64_t t, Req& r);
+  Instance make_instance(const Req& r) const;
+  void publish(uint64_t t, Req& r);
+  void ensure_grid();
   void launch_ready();
   void release(uint64_t t, Req& r);
   void reclaim_cancelled();
@@ -166,6 +264,32 @@ int ServeState::start() {
     // matrices, and the 32-bit solver path for packed instances)
     w.slot.pack = OT_SERVE_PACK != 0;
   }
+  // the persistent grid's queue, ring and head counter
+  pcap = max_inflight;
+  if (cudaHostAlloc(&pq, sizeof(PQueue), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc(&pring, sizeof(PItem) * size_t(pcap), cudaHostAllocMapped) != cudaSuccess ||
+      cudaMalloc(&dhead, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return OT_ERR_OOM;
+  }
+  std::memset(pq, 0, sizeof(PQueue));
+  if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&dpq), pq, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer(reinterpret_cast<void**>(&dpring), pring, 0) != cudaSuccess ||
+      cudaMemset(dhead, 0, sizeof(unsigned long long)) != cudaSuccess)
+    return OT_ERR_CUDA;
+  cudaStreamCreateWithFlags(&pstream, cudaStreamNonBlocking);
+  cudaEventCreateWithFlags(&pev, cudaEventDisableTiming);
+  psmem = group_bytes(kPTPI, kAlgoBKM, kPMaxCols, kPMaxCols);
+  if (cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(psmem)) != cudaSuccess)
+    return OT_ERR_CUDA;
+  {
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel, kPTPI, psmem) != cudaSuccess ||
+        per_sm < 1)
+      return OT_ERR_CUDA;
+    pgrid = per_sm * sms;
+  }
   if (cudaGetLastError() != cudaSuccess) return OT_ERR_CUDA;
   started = true;
   const int dev = ctx->device;
@@ -189,6 +313,51 @@ bool ServeState::try_admit(uint64_t, Req& r) {
   ++inflight;
   ++n_admitted;
   return true;
+}
+
+// The device descriptor of an admitted request (its arena block).
+Instance ServeState::make_instance(const Req& r) const {
+  Layout L(r.n, r.m);
+  char* b = arena.base + r.off;
+  Instance I = {};
+  I.C = reinterpret_cast<const int32_t*>(b + L.c);
+  I.ldc = r.m;
+  I.n = r.n;
+  I.m = r.m;
+  I.row_to_col = reinterpret_cast<int32_t*>(b + L.r2c);
+  I.u = reinterpret_cast<int64_t*>(b + L.u);
+  I.v = reinterpret_cast<int64_t*>(b + L.v);
+  I.cost = reinterpret_cast<int64_t*>(b + L.cost);
+  I.stats = reinterpret_cast<int64_t*>(b + L.stats);
+  I.status = dflags + r.flag;
+  I.step_limit = ctx->step_limit;
+  return I;
+}
+
+// Caller holds mu.  Hand request t (its matrix in the arena) to the
+// persistent grid: descriptor into the ring, then the tail, with release
+// order (the grid reads the tail with acquire order before the descriptor).
+void ServeState::publish(uint64_t t, Req& r) {
+  PItem& it = pring[ptail % static_cast<unsigned long long>(pcap)];
+  it.I = make_instance(r);
+  it.algo = r.algo;
+  it.pad = 0;
+  ++ptail;
+  __atomic_store_n(&pq->tail, ptail, __ATOMIC_RELEASE);
+  r.launched = true;
+  plive.push_back(t);
+}
+
+// Caller holds mu.  Launch the grid unless one is resident.  (Groups that
+// had already decided to leave may miss a request published meanwhile; the
+// serving thread then finds it unfinished with no grid resident and
+// launches again.)
+void ServeState::ensure_grid() {
+  if (prun && cudaEventQuery(pev) != cudaSuccess) return;  // still resident
+  serve_kernel<<<pgrid, kPTPI, psmem, pstream>>>(dpq, dpring, pcap, dhead);
+  cudaEventRecord(pev, pstream);
+  prun = true;
+  ++n_waves;
 }
 
 // Caller holds mu.  Return request t's arena block and status slot and
@@ -217,9 +386,27 @@ void ServeState::reclaim_cancelled() {
   }
 }
 
-// Caller holds mu.  Launch every admitted request as one wave.
+// Caller holds mu.  Requests the persistent grid takes are published at
+// once; every other admitted request is launched as one wave.
 void ServeState::launch_ready() {
   if (ready.empty()) return;
+  {
+    std::deque<uint64_t> rest;
+    bool any = false;
+    for (uint64_t t : ready) {
+      auto it = reqs.find(t);
+      if (it == reqs.end()) continue;
+      if (it->second.m <= kPMaxCols) {
+        publish(t, it->second);
+        any = true;
+      } else {
+        rest.push_back(t);
+      }
+    }
+    ready.swap(rest);
+    if (any) ensure_grid();
+    if (ready.empty()) return;
+  }
   Wave* w = nullptr;
   int busy = 0;
   for (Wave& x : waves) {
@@ -300,6 +487,17 @@ void ServeState::loop() {
     }
     launch_ready();
     reclaim_cancelled();
+    // published requests still unfinished while no grid is resident
+    if (!plive.empty()) {
+      std::vector<uint64_t> keep;
+      for (uint64_t t : plive) {
+        auto it = reqs.find(t);
+        if (it == reqs.end()) continue;
+        if (*reinterpret_cast<volatile int32_t*>(&flags[it->second.flag]) == kFlagPending) keep.push_back(t);
+      }
+      plive.swap(keep);
+      if (!plive.empty()) ensure_grid();
+    }
   }
 }
 
@@ -324,6 +522,14 @@ void serve_shutdown(ot_ctx* ctx) {
   s->cv.notify_all();
   if (s->th.joinable()) s->th.join();
   if (s->started) {
+    // the persistent grid leaves at its next pull (a request being solved
+    // is finished first)
+    if (s->pq) __atomic_store_n(&s->pq->stop, 1, __ATOMIC_RELEASE);
+    if (s->pstream) { cudaStreamSynchronize(s->pstream); cudaStreamDestroy(s->pstream); }
+    if (s->pev) cudaEventDestroy(s->pev);
+    if (s->dhead) cudaFree(s->dhead);
+    if (s->pring) cudaFreeHost(s->pring);
+    if (s->pq) cudaFreeHost(s->pq);
     for (Wave& w : s->waves) {
       if (w.busy) cudaEventSynchronize(w.done);
       w.slot.release();

@@ -68,7 +68,7 @@ def test_serving_full_size_range_against_oracle(oracle_mod, lib_path):
         assert _poll_all(served, pending, outs)
         cnt = ot.ot_serving_counters(served)
         assert cnt["completed"] == len(reqs)
-        assert cnt["waves"] >= 2
+        assert cnt["waves"] >= 1  # grid launches (requests of m <= 2048 join the resident grid)
         assert cnt["bytes_resident"] == 0
         for t, algo, C in tickets:
             r, c, u, v = (x.numpy() for x in outs[t])
