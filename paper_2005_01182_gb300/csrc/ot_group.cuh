@@ -253,11 +253,14 @@ __device__ __forceinline__ void solve_instance_v(const Instance& I, const GroupS
       L = S.misc[p];
     }
 
+    // bounded: at most m + 2 steps per phase, and no more than the caller's
+    // step cap allows (KM counts a phase's steps when it ends, batched KM
+    // one per level as it goes: the same number of guarded iterations)
+    long long glim = m + 2;
+    if (I.step_limit > 0 && I.step_limit - steps < glim) glim = I.step_limit - steps;
     int guard = 0;
     for (;;) {
-      // bounded: at most m + 2 steps per phase, and the caller's step cap
-      if (++guard > m + 2 ||
-          (I.step_limit > 0 && (ALGO == kAlgoKM ? steps + guard : steps + 1) > I.step_limit)) {
+      if (++guard > glim) {
         status = kDevStepLimit;
         break;
       }

@@ -177,3 +177,38 @@ def test_step_cap_times_out_one_instance(oracle_mod, lib_path):
         assert e.value.code == ot.OT_ERR_TIMEOUT
     finally:
         ctx.close()
+
+
+def test_serving_grid_relaunch_and_wide_requests(lib_path):
+    """Requests of m <= 2048 run on the resident serving grid, which leaves
+    after a spell without work and is launched again for later requests;
+    a request wider than 2048 columns takes a wave beside it.  Every result
+    equals the solo solve."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    first = [W.pixel_sqdist(n, seed=n) for n in (20, 130, 700)]
+    later = [W.pixel_sqdist(n, seed=n) for n in (45, 999)] + [W.pixel_sqdist(2100, 2150, seed=7)]
+    served = ot.Context(hbm_budget_bytes=512 << 20)
+    try:
+        outs = {}
+        pend = [(ot.ot_assign_submit(served, torch.from_numpy(C), ot.OT_KM), C) for C in first]
+        assert _poll_all(served, list(pend), outs, limit_s=120)
+        launches = ot.ot_serving_counters(served)["waves"]
+        time.sleep(1.0)  # long past the grid's idle limit: it has left
+        pend2 = [(ot.ot_assign_submit(served, torch.from_numpy(C), ot.OT_KM), C) for C in later]
+        assert _poll_all(served, list(pend2), outs, limit_s=300)
+        cnt = ot.ot_serving_counters(served)
+        assert cnt["waves"] >= launches + 2  # the grid again, and a wave for the wide request
+        assert cnt["completed"] == len(first) + len(later)
+        ref = ot.Context()
+        try:
+            for t, C in pend + pend2:
+                r, c, u, v = ot.ot_assign_solve(ref, torch.from_numpy(C).cuda(), ot.OT_KM)
+                torch.cuda.synchronize()
+                assert int(outs[t][1][0]) == int(c.item())
+                np.testing.assert_array_equal(outs[t][0].numpy(), r.cpu().numpy())
+                np.testing.assert_array_equal(outs[t][2].numpy(), u.cpu().numpy())
+        finally:
+            ref.close()
+    finally:
+        served.close()
