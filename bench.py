@@ -621,10 +621,12 @@ def main():
     ap.add_argument("--skip-extras", action="store_true")
     ap.add_argument("--served-requests", type=int, default=1500)
     ap.add_argument("--profile-once", default=None,
-                    choices=["batch", "auction", "n16384", "n8192", "sinkhorn16384", "sinkhorn8192"],
+                    choices=["batch", "auction", "n16384", "n8192", "n16384dense", "n8192dense", "sinkhorn16384",
+                             "sinkhorn8192"],
                     help="untimed single run for an ncu capture: 'batch' = autotune, then 3 batched "
                          "OT_AUTO calls on the 4096-instance batch inside an NVTX range 'timed'; "
-                         "'n16384' / 'n8192' = one batched-KM solve on a grid instance; "
+                         "'n16384' / 'n8192' = one batched-KM solve on a grid instance (sparse-list engine; "
+                         "'n16384dense' / 'n8192dense' on the dense cluster engine); "
                          "'sinkhorn16384' / 'sinkhorn8192' = log-domain Sinkhorn, eta = 2, 3 / 2 "
                          "fixed iterations on a 1024 x 1024-grid instance; 'auction' = one OT_AUCTION "
                          "solve of the 4096-instance batch inside an NVTX range 'timed'")
@@ -665,9 +667,12 @@ def main():
         print(json.dumps({"profile_once": args.profile_once, "cost": cost, "iterations": it}))
         ctx.close()
         return
-    if args.profile_once in ("n16384", "n8192"):
-        n = 16384 if args.profile_once == "n16384" else 8192
+    if args.profile_once in ("n16384", "n8192", "n16384dense", "n8192dense"):
+        n = 16384 if args.profile_once.startswith("n16384") else 8192
         C = W.grid_sqdist(n, n, grid=1024 if n == 16384 else 724)
+        if args.profile_once.endswith("dense"):
+            ctx.close()
+            ctx = ot.Context(device=local, flags=ot.OT_CFG_DENSE_WIDE)
         r, c, u, v, st = ot.ot_assign_solve_stats(ctx, torch.from_numpy(C).to(dev), ot.OT_BKM, stream)
         torch.cuda.synchronize()
         print(json.dumps({"profile_once": args.profile_once, "cost": int(c.item()), **st}))
