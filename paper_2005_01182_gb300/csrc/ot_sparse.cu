@@ -119,6 +119,7 @@ struct Ctl {
   int matched, done, status, phase;
   int scount, sbuf;
   long long lim;                 // min remaining budget of the list-relaxed rows of S
+  long long rescans;             // rows scanned densely inside the level search
   unsigned long long stats[8];   // levels, rows, bytes, phases, augs, init bytes
   unsigned long long prof[8];    // cycle accounting (profiling builds)
   unsigned long long sub[8];
@@ -326,6 +327,7 @@ __global__ void __launch_bounds__(kRelaxThreads) sp_init(Ws w) {
     c->scount = n;
     c->sbuf = 0;
     c->lim = kInf;
+    c->rescans = 0;
     for (int q = 0; q < 8; ++q) c->stats[q] = 0;
     for (int q = 0; q < 8; ++q) c->prof[q] = 0;
     for (int q = 0; q < 8; ++q) c->sub[q] = 0;
@@ -460,9 +462,11 @@ __device__ __forceinline__ Min2 block_min2(long long a, long long b, long long (
 // ---------------------------------------------------------------------------
 // the dependent search of one phase, augmentation and dual update
 // ---------------------------------------------------------------------------
-// Status of a phase whose levels would leave the 32-bit distance range of
-// the search (the solve is then redone on the dense cluster engine).
-constexpr int kRangeOut = -100;
+// Status of a phase that hands the solve to the dense cluster engine: its
+// levels would leave the 32-bit distance range of the search, or the lists
+// hold so few columns (heavily tied costs in a small range) that the search
+// has rescanned more than n rows densely itself, on one SM.
+constexpr int kToDense = -100;
 constexpr unsigned kSat32 = 0xffffffffu;
 constexpr unsigned kLevelMax = 0x7fffffffu;
 
@@ -476,7 +480,7 @@ __device__ __forceinline__ unsigned sat32(long long d) { return d < (long long)k
 // distance drops forgets its row), then, after a barrier, the candidates
 // that reached the final distance take the minimum row.  Every distance the
 // search compares at a level below 2^31 is exact; a phase whose next level
-// would be 2^31 or more stops with kRangeOut.
+// would be 2^31 or more stops with kToDense.
 __global__ void __launch_bounds__(kSearch, 1) sp_search(Ws w) {
   Ctl* ctl = w.ctl;
   if (ctl->done) return;
@@ -558,6 +562,7 @@ __global__ void __launch_bounds__(kSearch, 1) sp_search(Ws w) {
   int jcount = 0;
   int status = 0;
   unsigned long long levels = 0, rows = 0, bytes = 0;
+  long long rescans = 0;  // rows rescanned in this phase
   // candidates of this warp's first relaxed row, kept for the row step
   constexpr int kPer = kCap / 32;
   int cj[kPer];
@@ -588,6 +593,23 @@ __global__ void __launch_bounds__(kSearch, 1) sp_search(Ws w) {
       }
       __syncthreads();
       const int nr = s_nres < kRescanMax ? s_nres : kRescanMax;
+      rescans += nr;
+      // Lists too short for the instance (heavily tied costs in a small
+      // range): more than n/4 rows rescanned here at more than 4 per level,
+      // or 8 n in all.  Each rescan is a dense row pass on one SM, while the
+      // dense engine scans its rows on a whole cluster; measured at
+      // n = 4096, floor(C/16) of the circle/square instance needs about 25
+      // rescans per level (sparse 0.25 s, dense 0.05 s), circle/square and
+      // circle/triangle about 0.5 (either engine within 10 %, sparse faster
+      // on circle/square), the grids none.
+      {
+        const long long done_rows = ctl->rescans + rescans;
+        const long long done_levels = (long long)ctl->stats[0] + (long long)levels;
+        if ((done_rows > n / 4 && done_rows > 4 * done_levels) || done_rows > 8ll * n) {
+          status = kToDense;
+          break;
+        }
+      }
       for (int x = 0; x < nr; ++x) {
         const int i = s_resc[x];
         const long long ui = w.u[i], dr = w.drow[i];
@@ -639,7 +661,7 @@ __global__ void __launch_bounds__(kSearch, 1) sp_search(Ws w) {
       SP_PROF(2);
       continue;
     }
-    if (D > kLevelMax) { status = D == kSat32 ? kDevStepLimit : kRangeOut; break; }
+    if (D > kLevelMax) { status = D == kSat32 ? kDevStepLimit : kToDense; break; }
     // ---- the columns at level D join T; free ones end augmenting paths;
     // the warps holding them recompute their minimum ----
     if (wdist[wid] == D) {
@@ -838,6 +860,7 @@ __global__ void __launch_bounds__(kSearch, 1) sp_search(Ws w) {
     ctl->stats[1] += rows;
     ctl->stats[2] += bytes;
     ctl->stats[3] += 1;
+    ctl->rescans += rescans;
     if (status) {
       ctl->status = status;
       ctl->done = 1;
@@ -961,12 +984,12 @@ int solve_sparse(ot_ctx* ctx, const Instance& I, cudaStream_t stream, int64_t* s
   if (stats_out)
     for (int q = 0; q < 6; ++q) stats_out[q] = (int64_t)h.stats[q];
 #ifdef OT_SPARSE_PROFILE
-  std::fprintf(stderr, "sp_search cycles: min %llu rescan %llu pop %llu relax %llu augment+end %llu\n",
-               h.prof[1], h.prof[2], h.prof[3], h.prof[4], h.prof[5]);
+  std::fprintf(stderr, "sp_search cycles: min %llu rescan %llu pop %llu relax %llu augment+end %llu; rescanned rows %lld\n",
+               h.prof[1], h.prof[2], h.prof[3], h.prof[4], h.prof[5], h.rescans);
   std::fprintf(stderr, "relax, warp 0 from the step start: loads %llu v %llu distance step %llu row done %llu "
                "barrier %llu row step %llu\n", h.sub[0], h.sub[1], h.sub[2], h.sub[3], h.sub[4], h.sub[5]);
 #endif
-  if (h.status == kRangeOut) return solve_large(ctx, I, kAlgoBKM, stream, stats_out);
+  if (h.status == kToDense) return solve_large(ctx, I, kAlgoBKM, stream, stats_out);
   if (h.status || h.matched != n)
     return ctx_fail(ctx, OT_ERR_TIMEOUT, "sparse engine did not converge (status " + std::to_string(h.status) +
                                              ", matched " + std::to_string(h.matched) + " of " + std::to_string(n) +
