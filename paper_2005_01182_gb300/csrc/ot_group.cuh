@@ -95,10 +95,17 @@ __device__ __forceinline__ long long warp_min(long long x) {
   return x;
 }
 
+// CTA barrier without the .aligned qualifier: each thread first waits for
+// the other non-exited lanes of its warp, so the barrier stays correct when
+// the warp reaches it split by the data-dependent column branches before it
+// (the aligned form, __syncthreads, assumes a converged warp and may count a
+// split warp as arrived before its lane 0 stored its reduction slot).
+__device__ __forceinline__ void cta_sync() { asm volatile("barrier.sync 0;" ::: "memory"); }
+
 template <int TPI>
 __device__ __forceinline__ void group_sync() {
   if constexpr (TPI == 32) __syncwarp();
-  else __syncthreads();
+  else cta_sync();
 }
 
 // Shared-memory carve-up of one group.
@@ -155,9 +162,15 @@ __device__ __forceinline__ BestT<V> group_argmin(BestT<V> b, Best* slots, int& p
     BestT<V>* s = reinterpret_cast<BestT<V>*>(slots) + parity * NW;
     parity ^= 1;
     if (l == 0) s[w] = b;
-    __syncthreads();
-    BestT<V> c = (l < NW) ? s[l] : BestT<V>{inf_of<V>(), INT_MAX};
-    return warp_argmin(c);
+    cta_sync();
+    if constexpr (NW == 2) {
+      // two warps: every thread compares the two winners itself
+      const BestT<V> x = s[0], y = s[1];
+      return lex_less(y.d, y.j, x.d, x.j) ? y : x;
+    } else {
+      BestT<V> c = (l < NW) ? s[l] : BestT<V>{inf_of<V>(), INT_MAX};
+      return warp_argmin(c);
+    }
   }
 }
 
@@ -172,7 +185,7 @@ __device__ __forceinline__ long long group_sum(long long x, Best* slots, int& pa
     Best* s = slots + parity * NW;
     parity ^= 1;
     if (l == 0) s[w].d = x;
-    __syncthreads();
+    cta_sync();
     long long y = (l < NW) ? s[l].d : 0;
     return warp_sum(y);
   }
@@ -193,8 +206,17 @@ __device__ __forceinline__ void solve_instance_v(const Instance& I, const GroupS
   V dist[K], v[K];
   int pred[K];
   unsigned inT = 0;
+  // valid: the owned columns inside the instance; open (KM): valid and not
+  // in T, so that a step tests one bit per column
+  unsigned valid = 0;
 #pragma unroll
-  for (int k = 0; k < K; ++k) { v[k] = 0; dist[k] = kInfV; pred[k] = -1; }
+  for (int k = 0; k < K; ++k) {
+    v[k] = 0;
+    dist[k] = kInfV;
+    pred[k] = -1;
+    if (t + k * TPI < m) valid |= 1u << k;
+  }
+  unsigned open = valid;
 
   for (int i = t; i < n; i += TPI) { S.r2c[i] = -1; S.u[i] = 0; }
   for (int j = t; j < m; j += TPI) { S.c2r[j] = -1; S.pred[j] = -1; }
@@ -234,6 +256,7 @@ __device__ __forceinline__ void solve_instance_v(const Instance& I, const GroupS
 #pragma unroll
     for (int k = 0; k < K; ++k) { dist[k] = kInfV; pred[k] = -1; }
     inT = 0;
+    open = valid;
     int L = 1;
     int km_row = matched;  // KM roots rows in index order
     V level = 0;
@@ -268,19 +291,35 @@ __device__ __forceinline__ void solve_instance_v(const Instance& I, const GroupS
         if (t == 0) S.misc[p ^ 1] = 0;
       }
       // A1 / B2: scan the rows that just joined the tree, columns outside T
+      // (KM: fused with the thread's own minimum, A2)
+      V kbd = kInfV;
+      int kbj = INT_MAX;
       if constexpr (ALGO == kAlgoKM) {
         const int i = km_row;
         const V base = level - V(S.u[i]);
-        const int32_t* row = C + i * ldc;
-        const uint16_t* prow = P + (long long)i * m;
+        V c[K];
+        if (pk) {
+          const uint16_t* prow = P + unsigned(i) * unsigned(m);  // n * m < 2^31 on this engine
+#pragma unroll
+          for (int k = 0; k < K; ++k) c[k] = ((open >> k) & 1u) ? V(__ldg(prow + t + k * TPI)) : V(0);
+        } else {
+          const int32_t* row = C + i * ldc;
+#pragma unroll
+          for (int k = 0; k < K; ++k) c[k] = ((open >> k) & 1u) ? V(__ldg(row + t + k * TPI)) : V(0);
+        }
+        // columns in increasing order with strict comparisons: the lowest
+        // column among equal distances
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-          const int j = t + k * TPI;
-          if (j < m && !((inT >> k) & 1u)) {
-            const V cand = base + V(pk ? int(__ldg(prow + j)) : __ldg(row + j)) - v[k];
+          if ((open >> k) & 1u) {
+            const V cand = base + c[k] - v[k];
             if (cand < dist[k]) {
               dist[k] = cand;
               pred[k] = i;
+            }
+            if (dist[k] < kbd) {
+              kbd = dist[k];
+              kbj = t + k * TPI;
             }
           }
         }
@@ -327,11 +366,13 @@ __device__ __forceinline__ void solve_instance_v(const Instance& I, const GroupS
       }
 
       // A2 / B4: minimum distance outside T, lowest column on ties
-      BestT<V> b{kInfV, INT_MAX};
+      BestT<V> b{kbd, kbj};
+      if constexpr (ALGO == kAlgoBKM) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const int j = t + k * TPI;
-        if (j < m && !((inT >> k) & 1u) && lex_less(dist[k], j, b.d, b.j)) b = BestT<V>{dist[k], j};
+        for (int k = 0; k < K; ++k) {
+          const int j = t + k * TPI;
+          if (j < m && !((inT >> k) & 1u) && lex_less(dist[k], j, b.d, b.j)) b = BestT<V>{dist[k], j};
+        }
       }
       b = group_argmin<TPI, V>(b, S.slots, rpar);
       const V D = b.d;
@@ -346,7 +387,10 @@ __device__ __forceinline__ void solve_instance_v(const Instance& I, const GroupS
           for (int k = 0; k < K; ++k)
             if (k == ks) {
               S.pred[js] = pred[k];
-              if (mate >= 0) inT |= 1u << k;
+              if (mate >= 0) {
+                inT |= 1u << k;
+                open &= ~(1u << k);
+              }
             }
         }
         if (mate >= 0) {
@@ -560,9 +604,9 @@ __global__ void OT_GROUP_BOUNDS(TPI)
       idx = __shfl_sync(0xffffffffu, x, 0);
     } else {
       if (t == 0) S.misc[15] = atomicAdd(work, 1);
-      __syncthreads();
+      cta_sync();
       idx = S.misc[15];
-      __syncthreads();
+      cta_sync();
     }
     if (idx >= num) break;
     const Instance I = insts[order ? order[idx] : idx];
