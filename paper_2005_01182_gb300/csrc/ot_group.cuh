@@ -206,17 +206,11 @@ __device__ __forceinline__ void solve_instance_v(const Instance& I, const GroupS
   V dist[K], v[K];
   int pred[K];
   unsigned inT = 0;
-  // valid: the owned columns inside the instance; open (KM): valid and not
-  // in T, so that a step tests one bit per column
-  unsigned valid = 0;
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    v[k] = 0;
-    dist[k] = kInfV;
-    pred[k] = -1;
-    if (t + k * TPI < m) valid |= 1u << k;
-  }
-  unsigned open = valid;
+  for (int k = 0; k < K; ++k) { v[k] = 0; dist[k] = kInfV; pred[k] = -1; }
+  // KM's open columns: owned, inside the instance and outside T (recomputed
+  // per step: a mask kept in registers costs the register-bound groups more)
+  const auto is_open = [&](int k) -> bool { return t + k * TPI < m && !((inT >> k) & 1u); };
 
   for (int i = t; i < n; i += TPI) { S.r2c[i] = -1; S.u[i] = 0; }
   for (int j = t; j < m; j += TPI) { S.c2r[j] = -1; S.pred[j] = -1; }
@@ -256,7 +250,6 @@ __device__ __forceinline__ void solve_instance_v(const Instance& I, const GroupS
 #pragma unroll
     for (int k = 0; k < K; ++k) { dist[k] = kInfV; pred[k] = -1; }
     inT = 0;
-    open = valid;
     int L = 1;
     int km_row = matched;  // KM roots rows in index order
     V level = 0;
@@ -301,17 +294,17 @@ __device__ __forceinline__ void solve_instance_v(const Instance& I, const GroupS
         if (pk) {
           const uint16_t* prow = P + unsigned(i) * unsigned(m);  // n * m < 2^31 on this engine
 #pragma unroll
-          for (int k = 0; k < K; ++k) c[k] = ((open >> k) & 1u) ? V(__ldg(prow + t + k * TPI)) : V(0);
+          for (int k = 0; k < K; ++k) c[k] = is_open(k) ? V(__ldg(prow + t + k * TPI)) : V(0);
         } else {
           const int32_t* row = C + i * ldc;
 #pragma unroll
-          for (int k = 0; k < K; ++k) c[k] = ((open >> k) & 1u) ? V(__ldg(row + t + k * TPI)) : V(0);
+          for (int k = 0; k < K; ++k) c[k] = is_open(k) ? V(__ldg(row + t + k * TPI)) : V(0);
         }
         // columns in increasing order with strict comparisons: the lowest
         // column among equal distances
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-          if ((open >> k) & 1u) {
+          if (is_open(k)) {
             const V cand = base + c[k] - v[k];
             if (cand < dist[k]) {
               dist[k] = cand;
@@ -387,10 +380,7 @@ __device__ __forceinline__ void solve_instance_v(const Instance& I, const GroupS
           for (int k = 0; k < K; ++k)
             if (k == ks) {
               S.pred[js] = pred[k];
-              if (mate >= 0) {
-                inT |= 1u << k;
-                open &= ~(1u << k);
-              }
+              if (mate >= 0) inT |= 1u << k;
             }
         }
         if (mate >= 0) {
