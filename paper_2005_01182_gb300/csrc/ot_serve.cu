@@ -10,7 +10,11 @@
 // on several streams.  Each request finishes on its own: the solver group
 // writes the results and then, after a system-scope fence, a status word in
 // mapped host memory, which poll() reads.  poll() copies the results out and
-// frees the arena block, which lets queued requests in.
+// frees the arena block, which lets queued requests in.  Requests on the
+// persistent grid write their results (assignment, duals, cost, counters)
+// straight into a slot of mapped pinned host memory, so that poll() of a
+// finished grid request is a host copy with no CUDA call; when every slot
+// is taken a request writes them into its arena block instead.
 #include <algorithm>
 
 #ifndef OT_SERVE_PACK
@@ -87,6 +91,7 @@ struct Req {
   int n = 0, m = 0, algo = 0;
   size_t bytes = 0, off = 0;
   int flag = -1;                 // slot in the mapped status array
+  int res = -1;                  // slot in the mapped result pool (grid requests), or -1
   bool admitted = false, launched = false;
   bool submitting = true;        // submit() has not returned the ticket yet
   bool cancelled = false;        // cancelled while its wave runs: reclaimed once finished
@@ -127,6 +132,20 @@ struct Layout {
 constexpr int kPTPI = 512, kPK = 4;
 constexpr int kPMaxCols = kPTPI * kPK;
 constexpr int kIdlePolls = 1 << 14;
+
+// Mapped result pool of the persistent grid: kResSlots slots, each holding
+// the results of one request of m <= kPMaxCols (41.5 KB; 42.5 MB of pinned
+// host memory in all).
+constexpr int kResSlots = 1024;
+struct ResLayout {
+  static constexpr size_t r2c = 0;
+  static constexpr size_t u = r2c + 4 * size_t(kPMaxCols);
+  static constexpr size_t v = u + 8 * size_t(kPMaxCols);
+  static constexpr size_t cost = v + 8 * size_t(kPMaxCols);
+  static constexpr size_t stats = cost + 256;
+  static constexpr size_t total = stats + 256;
+};
+static_assert(ResLayout::total % 256 == 0, "result slots stay 256-byte aligned");
 
 struct PQueue {                    // mapped pinned host memory
   unsigned long long tail;         // requests published (written by the host)
@@ -228,6 +247,9 @@ struct ServeState {
   unsigned long long ptail = 0;         // requests published
   cudaStream_t pstream = nullptr;
   cudaEvent_t pev = nullptr;            // end of the latest grid launch
+  char* hres = nullptr;                 // mapped result pool (host address)
+  char* dres = nullptr;                 // its device address
+  std::vector<int> free_res;
   bool prun = false;
   int pgrid = 0;
   size_t psmem = 0;
@@ -273,6 +295,12 @@ int ServeState::start() {
     return OT_ERR_OOM;
   }
   std::memset(pq, 0, sizeof(PQueue));
+  if (cudaHostAlloc(&hres, ResLayout::total * kResSlots, cudaHostAllocMapped) != cudaSuccess) {
+    cudaGetLastError();
+    return OT_ERR_OOM;
+  }
+  if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&dres), hres, 0) != cudaSuccess) return OT_ERR_CUDA;
+  for (int i = kResSlots - 1; i >= 0; --i) free_res.push_back(i);
   if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&dpq), pq, 0) != cudaSuccess ||
       cudaHostGetDevicePointer(reinterpret_cast<void**>(&dpring), pring, 0) != cudaSuccess ||
       cudaMemset(dhead, 0, sizeof(unsigned long long)) != cudaSuccess)
@@ -339,7 +367,18 @@ Instance ServeState::make_instance(const Req& r) const {
 // order (the grid reads the tail with acquire order before the descriptor).
 void ServeState::publish(uint64_t t, Req& r) {
   PItem& it = pring[ptail % static_cast<unsigned long long>(pcap)];
-  it.I = make_instance(r);
+  Instance I = make_instance(r);
+  if (!free_res.empty()) {
+    r.res = free_res.back();
+    free_res.pop_back();
+    char* b = dres + size_t(r.res) * ResLayout::total;
+    I.row_to_col = reinterpret_cast<int32_t*>(b + ResLayout::r2c);
+    I.u = reinterpret_cast<int64_t*>(b + ResLayout::u);
+    I.v = reinterpret_cast<int64_t*>(b + ResLayout::v);
+    I.cost = reinterpret_cast<int64_t*>(b + ResLayout::cost);
+    I.stats = reinterpret_cast<int64_t*>(b + ResLayout::stats);
+  }
+  it.I = I;
   it.algo = r.algo;
   it.pad = 0;
   ++ptail;
@@ -368,6 +407,7 @@ void ServeState::release(uint64_t t, Req& r) {
     free_flags.push_back(r.flag);
     --inflight;
   }
+  if (r.res >= 0) free_res.push_back(r.res);
   reqs.erase(t);
 }
 
@@ -529,6 +569,7 @@ void serve_shutdown(ot_ctx* ctx) {
     if (s->pev) cudaEventDestroy(s->pev);
     if (s->dhead) cudaFree(s->dhead);
     if (s->pring) cudaFreeHost(s->pring);
+    if (s->hres) cudaFreeHost(s->hres);
     if (s->pq) cudaFreeHost(s->pq);
     for (Wave& w : s->waves) {
       if (w.busy) cudaEventSynchronize(w.done);
@@ -579,14 +620,13 @@ int ot_assign_submit(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int3
   // request that could not be admitted keeps a packed host copy.
   std::vector<int32_t> hc;
   cudaError_t e;
-  if (now) {
-    e = cudaMemcpy2DAsync(dst, 4 * size_t(m), C, 4 * size_t(ldc), 4 * size_t(m), n, cudaMemcpyDefault,
+  if (!now) hc.resize(size_t(n) * m);
+  void* to = now ? static_cast<void*>(dst) : static_cast<void*>(hc.data());
+  if (ldc == m)  // contiguous rows: one linear copy
+    e = cudaMemcpyAsync(to, C, 4 * size_t(n) * m, cudaMemcpyDefault, s->poll_stream);
+  else
+    e = cudaMemcpy2DAsync(to, 4 * size_t(m), C, 4 * size_t(ldc), 4 * size_t(m), n, cudaMemcpyDefault,
                           s->poll_stream);
-  } else {
-    hc.resize(size_t(n) * m);
-    e = cudaMemcpy2DAsync(hc.data(), 4 * size_t(m), C, 4 * size_t(ldc), 4 * size_t(m), n,
-                          cudaMemcpyDefault, s->poll_stream);
-  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->poll_stream);
   lk.lock();
   Req& rr = s->reqs[t];
@@ -622,16 +662,37 @@ int ot_assign_poll(ot_ctx* ctx, uint64_t ticket, int32_t* row_to_col, int64_t* c
   Req& r = it->second;
   if (r.cancelled || r.submitting) return ctx_fail(ctx, OT_ERR_TICKET, "unknown ticket");
   if (!r.launched) return OT_PENDING;
-  const int32_t f = *reinterpret_cast<volatile int32_t*>(&s->flags[r.flag]);
+  // acquire: the results, written before the status word, are visible
+  const int32_t f = __atomic_load_n(&s->flags[r.flag], __ATOMIC_ACQUIRE);
   if (f == kFlagPending) return OT_PENDING;
   const int n = r.n, m = r.m;
   char* b = s->arena.base + r.off;
   const size_t off = r.off, bytes = r.bytes;
-  const int flag = r.flag;
+  const int flag = r.flag, res = r.res;
   lk.unlock();
-  cudaSetDevice(ctx->device);
   int rc = f;
-  if (f == OT_OK) {
+  if (f == OT_OK && res >= 0) {
+    // results in the mapped pool: host copies (a device destination takes
+    // one synchronous copy each)
+    const char* h = s->hres + size_t(res) * ResLayout::total;
+    const void* src[4] = {h + ResLayout::r2c, h + ResLayout::cost, h + ResLayout::u, h + ResLayout::v};
+    void* dst[4] = {row_to_col, cost, u, v};
+    const size_t len[4] = {4 * size_t(n), 8, 8 * size_t(n), 8 * size_t(m)};
+    for (int q = 0; q < 4 && rc == OT_OK; ++q) {
+      if (!dst[q]) continue;
+      cudaPointerAttributes a;
+      const bool dev = cudaPointerGetAttributes(&a, dst[q]) == cudaSuccess && a.type == cudaMemoryTypeDevice;
+      cudaGetLastError();
+      if (!dev) {
+        std::memcpy(dst[q], src[q], len[q]);
+      } else {
+        cudaSetDevice(ctx->device);
+        const cudaError_t e = cudaMemcpy(dst[q], src[q], len[q], cudaMemcpyDefault);
+        if (e != cudaSuccess) rc = ctx_cuda(ctx, e, "poll copy");
+      }
+    }
+  } else if (f == OT_OK) {
+    cudaSetDevice(ctx->device);
     Layout L(n, m);
     cudaError_t e = cudaSuccess;
     if (row_to_col) e = cudaMemcpyAsync(row_to_col, b + L.r2c, 4 * size_t(n), cudaMemcpyDefault, s->poll_stream);
@@ -644,6 +705,7 @@ int ot_assign_poll(ot_ctx* ctx, uint64_t ticket, int32_t* row_to_col, int64_t* c
   lk.lock();
   s->arena.release(off, bytes);
   s->free_flags.push_back(flag);
+  if (res >= 0) s->free_res.push_back(res);
   --s->inflight;
   s->reqs.erase(ticket);
   if (rc == OT_OK) ++s->n_completed;
