@@ -494,9 +494,11 @@ def measure_served(ctx_unused, stream, ot, torch, dev, args):
     [16, 2048], squared pixel distances on a 28 x 28 grid) through
     ot_assign_submit / ot_assign_poll, at 0.5x and 0.9x of the measured
     saturated throughput; p50/p99 latency from arrival to completion.  The
-    stream is three times as long as the set of matrices it cycles over;
-    every served cost is checked against the matrix's solo solve."""
-    import threading
+    stream is ten times as long as the set of matrices it cycles over;
+    every served cost is checked against the matrix's solo solve.  Steady
+    throughput: completions over arrivals within one window (after the
+    first tenth of the arrivals, up to the last arrival), so that neither
+    the start nor the drain after the last arrival counts."""
     nreq = args.served_requests
     reqs = W.served_requests(nreq, rate_per_s=1.0, seed=W.BASE_SEED + 7)
     mats = [torch.from_numpy(C).pin_memory() for _, C in reqs]
@@ -511,33 +513,30 @@ def measure_served(ctx_unused, stream, ot, torch, dev, args):
 
     # the stream: `nstream` requests cycling over the nreq matrices, unit-rate
     # Poisson arrival times scaled by the offered rate
-    nstream = 3 * nreq
+    nstream = 10 * nreq
     unit_t = np.cumsum(np.random.default_rng(W.BASE_SEED + 8).exponential(1.0, size=nstream))
     unit_t -= unit_t[0]
     outs = [(torch.empty(mats[k % nreq].shape[0], dtype=torch.int32), torch.empty(1, dtype=torch.int64), None, None)
             for k in range(nstream)]
 
     def run(rate):
+        """One client thread, as an asynchronous serving front end runs it:
+        submit every request whose arrival time has passed, sweep the live
+        tickets once, sleep only when there is nothing to do.  rate None:
+        saturation, with at most `window` requests outstanding (submitted,
+        not yet collected)."""
         sctx = ot.Context(hbm_budget_bytes=8 << 30, wave_streams=4, tune_file=tune_path)
         arrivals = unit_t / rate if rate else np.zeros(nstream)
+        window = nstream if rate else 1024
         done_t = [None] * nstream
         tickets = [None] * nstream
         t0 = time.perf_counter()
-
-        def submitter():
-            for i in range(nstream):
-                if rate:
-                    d = arrivals[i] - (time.perf_counter() - t0)
-                    if d > 0:
-                        time.sleep(d)
-                tickets[i] = ot.ot_assign_submit(sctx, mats[i % nreq], ot.OT_AUTO)
-
-        th = threading.Thread(target=submitter)
-        th.start()
         nxt = 0
         live = []
         while nxt < nstream or live:
-            while nxt < nstream and tickets[nxt] is not None:
+            now = time.perf_counter() - t0
+            while nxt < nstream and arrivals[nxt] <= now and len(live) < window:
+                tickets[nxt] = ot.ot_assign_submit(sctx, mats[nxt % nreq], ot.OT_AUTO)
                 live.append(nxt)
                 nxt += 1
             rest = []
@@ -546,12 +545,14 @@ def measure_served(ctx_unused, stream, ot, torch, dev, args):
                     done_t[i] = time.perf_counter() - t0
                 else:
                     rest.append(i)
-            # a sweep that finished nothing yields the GIL and the serving
-            # lock to the submitting thread for a moment
             if len(rest) == len(live):
-                time.sleep(0.00005)
+                # nothing finished: wait a little, not past the next arrival
+                wait = 5e-5
+                if nxt < nstream and len(rest) < window:
+                    wait = min(wait, arrivals[nxt] - (time.perf_counter() - t0))
+                if wait > 0:
+                    time.sleep(wait)
             live = rest
-        th.join()
         total = time.perf_counter() - t0
         cnt = ot.ot_serving_counters(sctx)
         sctx.close()
@@ -561,12 +562,14 @@ def measure_served(ctx_unused, stream, ot, torch, dev, args):
                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                "grid_or_wave_launches": cnt["waves"]}
         if rate:
-            # completions while requests were still arriving, per second: the
-            # rate the loop keeps up with (the drain after the last arrival
-            # is excluded)
-            last = float(arrivals[-1])
-            res["steady_solves_per_s"] = float((done <= last).sum()) / last
-            res["steady_over_offered"] = res["steady_solves_per_s"] / rate
+            # the rate the loop keeps up with: completions within the window
+            # over arrivals within it (equal when it keeps up, whatever the
+            # latency)
+            lo, hi = float(arrivals[nstream // 10]), float(arrivals[-1])
+            n_arr = float(((arrivals >= lo) & (arrivals <= hi)).sum())
+            n_done = float(((done >= lo) & (done <= hi)).sum())
+            res["steady_solves_per_s"] = n_done / (hi - lo)
+            res["steady_over_offered"] = n_done / n_arr
         return res
 
     # the cost of every request solved alone (one batched call on the device,
