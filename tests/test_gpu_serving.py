@@ -212,3 +212,59 @@ def test_serving_grid_relaunch_and_wide_requests(lib_path):
             ref.close()
     finally:
         served.close()
+
+
+def test_serving_result_paths_and_destinations(lib_path):
+    """Requests on the resident grid write their results into mapped host
+    slots (1024 of them); once every slot is held by an uncollected request
+    the next ones write into their device blocks instead.  1100 small
+    requests are submitted before any is polled, so both paths run; they are
+    polled into device, pinned and pageable tensors in turn, beside a request
+    wider than 2048 columns (a wave).  Every result equals the batched solo
+    solve bit for bit."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rng = np.random.default_rng(77)
+    mats = [W.pixel_sqdist(int(n), seed=int(s)) for n, s in zip(rng.integers(16, 41, size=1100), range(1100))]
+    mats.append(W.pixel_sqdist(2060, 2100, seed=5))
+    served = ot.Context(hbm_budget_bytes=1 << 30)
+    ref = ot.Context()
+    try:
+        tickets = [ot.ot_assign_submit(served, torch.from_numpy(C), ot.OT_KM) for C in mats]
+        b = ot.ot_assign_solve_batched(ref, [torch.from_numpy(C).cuda() for C in mats], ot.OT_KM)
+        torch.cuda.synchronize()
+        assert (b.status.cpu().numpy() == 0).all()
+        kinds = ("cuda", "pinned", "pageable")
+        pending = list(range(len(mats)))
+        got = {}
+        t0 = time.time()
+        while pending and time.time() - t0 < 300:
+            rest = []
+            for q in pending:
+                n, m = mats[q].shape
+                kind = kinds[q % 3]
+                o = [torch.empty(n, dtype=torch.int32), torch.empty(1, dtype=torch.int64),
+                     torch.empty(n, dtype=torch.int64), torch.empty(m, dtype=torch.int64)]
+                if kind == "cuda":
+                    o = [x.cuda() for x in o]
+                elif kind == "pinned":
+                    o = [x.pin_memory() for x in o]
+                if ot.ot_assign_poll(served, tickets[q], tuple(o)) == ot.OT_OK:
+                    got[q] = o
+                else:
+                    rest.append(q)
+            pending = rest
+            if pending:
+                time.sleep(0.001)
+        assert not pending
+        torch.cuda.synchronize()
+        for q in range(len(mats)):
+            r, c, u, v = (x.cpu().numpy() for x in got[q])
+            assert int(c[0]) == int(b.cost[q])
+            np.testing.assert_array_equal(r, b.outs[q][0].cpu().numpy())
+            np.testing.assert_array_equal(u, b.outs[q][1].cpu().numpy())
+            np.testing.assert_array_equal(v, b.outs[q][2].cpu().numpy())
+        assert ot.ot_serving_counters(served)["completed"] == len(mats)
+    finally:
+        served.close()
+        ref.close()
