@@ -521,38 +521,34 @@ def measure_served(ctx_unused, stream, ot, torch, dev, args):
 
     def run(rate):
         """One client thread, as an asynchronous serving front end runs it:
-        submit every request whose arrival time has passed, sweep the live
-        tickets once, sleep only when there is nothing to do.  rate None:
-        saturation, with at most `window` requests outstanding (submitted,
-        not yet collected)."""
+        submit every request whose arrival time has passed, collect the
+        requests the completion query returns, sleep only when there is
+        nothing to do.  rate None: saturation, with at most `window`
+        requests outstanding (submitted, not yet collected)."""
         sctx = ot.Context(hbm_budget_bytes=8 << 30, wave_streams=4, tune_file=tune_path)
         arrivals = unit_t / rate if rate else np.zeros(nstream)
         window = nstream if rate else 1024
         done_t = [None] * nstream
-        tickets = [None] * nstream
         t0 = time.perf_counter()
         nxt = 0
-        live = []
-        while nxt < nstream or live:
+        tix = {}  # ticket -> request index, while outstanding
+        while nxt < nstream or tix:
             now = time.perf_counter() - t0
-            while nxt < nstream and arrivals[nxt] <= now and len(live) < window:
-                tickets[nxt] = ot.ot_assign_submit(sctx, mats[nxt % nreq], ot.OT_AUTO)
-                live.append(nxt)
+            while nxt < nstream and arrivals[nxt] <= now and len(tix) < window:
+                tix[ot.ot_assign_submit(sctx, mats[nxt % nreq], ot.OT_AUTO)] = nxt
                 nxt += 1
-            rest = []
-            for i in live:
-                if ot.ot_assign_poll(sctx, tickets[i], outs[i]) == ot.OT_OK:
-                    done_t[i] = time.perf_counter() - t0
-                else:
-                    rest.append(i)
-            if len(rest) == len(live):
+            fin = ot.ot_assign_completed(sctx)
+            for tk in fin:
+                i = tix.pop(tk)
+                assert ot.ot_assign_poll(sctx, tk, outs[i]) == ot.OT_OK
+                done_t[i] = time.perf_counter() - t0
+            if not fin:
                 # nothing finished: wait a little, not past the next arrival
                 wait = 5e-5
-                if nxt < nstream and len(rest) < window:
+                if nxt < nstream and len(tix) < window:
                     wait = min(wait, arrivals[nxt] - (time.perf_counter() - t0))
                 if wait > 0:
                     time.sleep(wait)
-            live = rest
         total = time.perf_counter() - t0
         cnt = ot.ot_serving_counters(sctx)
         sctx.close()

@@ -261,6 +261,15 @@ int ot_assign_submit(ot_ctx* ctx, const int32_t* C, int64_t ldc, int32_t n, int3
 int ot_assign_poll(ot_ctx* ctx, uint64_t ticket, int32_t* row_to_col, int64_t* cost,
                    int64_t* u, int64_t* v);
 
+/* Completion query: the tickets of requests whose solve has ended (with a
+ * result or an error) and that no earlier call returned, at most `max` of
+ * them, into tickets[0 .. *count - 1] (host array).  Each is then collected
+ * with ot_assign_poll, which does not answer OT_PENDING for it.  Requests
+ * still waiting or running, and collected or cancelled ones, are not
+ * returned.  A client that collects through this call does work in
+ * proportion to the completions, not to the requests in flight. */
+int ot_assign_completed(ot_ctx* ctx, uint64_t* tickets, int32_t max, int32_t* count);
+
 /* Cancel a submitted request: its result is discarded and its ticket
  * retired (a later poll or cancel returns OT_ERR_TICKET).  A request still
  * waiting for admission, or admitted but not yet launched, is dropped at

@@ -254,6 +254,7 @@ struct ServeState {
   int pgrid = 0;
   size_t psmem = 0;
   std::vector<uint64_t> plive;          // published, status not yet seen final
+  std::vector<uint64_t> watch;          // launched, not yet returned by ot_assign_completed
 
   int start();
   void loop();
@@ -385,6 +386,7 @@ void ServeState::publish(uint64_t t, Req& r) {
   __atomic_store_n(&pq->tail, ptail, __ATOMIC_RELEASE);
   r.launched = true;
   plive.push_back(t);
+  watch.push_back(t);
 }
 
 // Caller holds mu.  Launch the grid unless one is resident.  (Groups that
@@ -492,7 +494,10 @@ void ServeState::launch_ready() {
       for (int i : unsup) flags[reqs[ids[i]].flag] = OT_ERR_UNSUPPORTED;
     }
   }
-  for (uint64_t t : tk) reqs[t].launched = true;
+  for (uint64_t t : tk) {
+    reqs[t].launched = true;
+    watch.push_back(t);
+  }
   cudaEventRecord(w->done, w->stream);
   w->busy = true;
   ++n_waves;
@@ -713,6 +718,28 @@ int ot_assign_poll(ot_ctx* ctx, uint64_t ticket, int32_t* row_to_col, int64_t* c
   s->cv.notify_one();
   if (rc != OT_OK && rc != OT_ERR_CUDA) return ctx_fail(ctx, rc, "request failed on the device");
   return rc;
+}
+
+int ot_assign_completed(ot_ctx* ctx, uint64_t* tickets, int32_t max, int32_t* count) {
+  if (!ctx || !count || max < 0 || (max > 0 && !tickets)) return OT_ERR_ARG;
+  ServeState* s = ctx->serve;
+  std::lock_guard<std::mutex> g(s->mu);
+  int c = 0;
+  size_t keep = 0;
+  for (size_t q = 0; q < s->watch.size(); ++q) {
+    const uint64_t t = s->watch[q];
+    auto it = s->reqs.find(t);
+    if (it == s->reqs.end() || it->second.cancelled) continue;  // collected or cancelled: dropped
+    // acquire: the results, written before the status word, are visible
+    if (c < max && __atomic_load_n(&s->flags[it->second.flag], __ATOMIC_ACQUIRE) != kFlagPending) {
+      tickets[c++] = t;
+      continue;
+    }
+    s->watch[keep++] = t;
+  }
+  s->watch.resize(keep);
+  *count = c;
+  return OT_OK;
 }
 
 int ot_assign_cancel(ot_ctx* ctx, uint64_t ticket) {

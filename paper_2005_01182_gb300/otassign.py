@@ -93,6 +93,7 @@ def load(path: str | None = None):
         "ot_assign_poll": (ctypes.c_int, [vp, ctypes.c_uint64, vp, vp, vp, vp]),
         "ot_assign_drain": (ctypes.c_int, [vp]),
         "ot_assign_cancel": (ctypes.c_int, [vp, ctypes.c_uint64]),
+        "ot_assign_completed": (ctypes.c_int, [vp, vp, ctypes.c_int32, vp]),
         "ot_serving_counters": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
         "ot_autotune": (ctypes.c_int, [vp, i32, pp, ctypes.POINTER(i64), ctypes.POINTER(i32),
                                        ctypes.POINTER(i32), i32, i32]),
@@ -397,6 +398,18 @@ def ot_assign_poll(ctx: Context, ticket: int, out) -> int:
         return OT_PENDING
     ctx._raise(rc, "ot_assign_poll")
     return OT_OK
+
+
+def ot_assign_completed(ctx: Context, max_count: int = 4096) -> list:
+    """Tickets whose solve has ended since the last call (collect each with
+    ot_assign_poll, which then returns OT_OK or raises)."""
+    buf = getattr(ctx, "_done_buf", None)
+    if buf is None or len(buf) < max_count:
+        buf = (ctypes.c_uint64 * max_count)()
+        ctx._done_buf = buf
+    cnt = ctypes.c_int32()
+    ctx._raise(ctx.lib.ot_assign_completed(ctx.h, buf, max_count, ctypes.byref(cnt)), "ot_assign_completed")
+    return buf[: cnt.value]
 
 
 def ot_assign_cancel(ctx: Context, ticket: int):

@@ -268,3 +268,52 @@ def test_serving_result_paths_and_destinations(lib_path):
     finally:
         served.close()
         ref.close()
+
+
+def test_completion_query_returns_each_request_once(oracle_mod, lib_path):
+    """ot_assign_completed returns every finished request exactly once (three
+    at most per call here), never a cancelled one, then nothing; results
+    collected through it equal the oracle's KM (small requests) or the solo
+    solve (the rest, a wave-sized one included) bit for bit."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sizes = (16, 33, 70, 150, 300, 700, 1200, 2100)
+    mats = [W.pixel_sqdist(n, seed=400 + n) for n in sizes]
+    served = ot.Context(hbm_budget_bytes=512 << 20)
+    ref = ot.Context()
+    try:
+        tickets = [ot.ot_assign_submit(served, torch.from_numpy(C), ot.OT_KM) for C in mats]
+        gone = ot.ot_assign_submit(served, torch.from_numpy(W.pixel_sqdist(500, seed=1)), ot.OT_KM)
+        ot.ot_assign_cancel(served, gone)
+        seen, outs = [], {}
+        t0 = time.time()
+        while len(seen) < len(mats) and time.time() - t0 < 300:
+            got = ot.ot_assign_completed(served, 3)
+            assert len(got) <= 3
+            for tk in got:
+                q = tickets.index(tk)
+                n, m = mats[q].shape
+                o = _host_out(n, m)
+                assert ot.ot_assign_poll(served, tk, o) == ot.OT_OK
+                seen.append(tk)
+                outs[q] = o
+            if not got:
+                time.sleep(0.001)
+        assert sorted(seen) == sorted(tickets) and len(set(seen)) == len(seen)
+        assert gone not in seen
+        assert ot.ot_assign_completed(served) == []
+        for q, C in enumerate(mats):
+            r, c, u, v = (x.numpy() for x in outs[q])
+            if C.shape[0] <= 300:
+                a0, c0, u0, v0 = oracle_mod.km(C)
+            else:
+                a0, c0, u0, v0 = (x.cpu().numpy() if hasattr(x, "cpu") else x
+                                  for x in ot.ot_assign_solve(ref, torch.from_numpy(C).cuda(), ot.OT_KM))
+                c0 = int(np.asarray(c0).reshape(-1)[0])
+            assert int(c[0]) == c0
+            np.testing.assert_array_equal(r, a0)
+            np.testing.assert_array_equal(u, u0)
+            np.testing.assert_array_equal(v, v0)
+    finally:
+        served.close()
+        ref.close()
