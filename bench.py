@@ -67,9 +67,10 @@ def kernel_source_hash(read=None) -> str:
 
 
 def measured_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    """DRAM bytes per launch of `kernel` ("<name> instances <count>": the
+    launch and the instance set it ran) from the committed ncu summary, if
     it was taken on the kernel sources as they are now (else None).  Lines:
-    `traffic <kernel> <bytes per launch> source <sha256>`."""
+    `traffic <name> instances <count> <bytes per launch> source <sha256>`."""
     p = os.path.join(ROOT, "profiles", "batch4096_embed_traffic.md")
     if not os.path.exists(p):
         return None
@@ -84,10 +85,10 @@ def measured_traffic(kernel: str):
 
 
 def measured_instructions(kernel: str):
-    """Warp instructions per launch of `kernel` (ncu smsp__inst_executed.sum)
-    from the committed summary, if taken on the kernel sources as they are
-    now (else None).  Lines: `issue <kernel> <instructions per launch> source
-    <sha256>`."""
+    """Warp instructions per launch of `kernel` ("<name> instances <count>")
+    (ncu smsp__inst_executed.sum) from the committed summary, if taken on the
+    kernel sources as they are now (else None).  Lines: `issue <name>
+    instances <count> <instructions per launch> source <sha256>`."""
     p = os.path.join(ROOT, "profiles", "batch4096_embed_traffic.md")
     if not os.path.exists(p):
         return None
@@ -808,12 +809,13 @@ def main():
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
         sm_mhz = clocks.get("sm_mhz") or 2070.0
         issue_peak = nsm * 4 * sm_mhz * 1e6
-        inst = measured_instructions(dom_name)
+        dom_key = "%s instances %d" % (dom_name, dom["instances"])
+        inst = measured_instructions(dom_key)
         issue_rate = inst / (dom_ms / 1000.0) if inst else None
         roofline = {"bound": "alu", "achieved": issue_rate / 1e9 if inst else None,
                     "peak": issue_peak / 1e9, "unit": "G warp instructions/s",
                     "frac": issue_rate / issue_peak if inst else None,
-                    "traffic": measured_traffic(dom_name), "kernel": dom_name,
+                    "traffic": measured_traffic(dom_key), "kernel": dom_name,
                     "peak_kind": f"{nsm} SMs x 4 schedulers x 1 warp instruction/cycle at the sampled "
                                  f"median SM clock ({sm_mhz:.0f} MHz)",
                     "warp_instructions_per_launch": inst, "launch_ms": dom_ms,
