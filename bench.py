@@ -621,6 +621,9 @@ def main():
     ap.add_argument("--sample", type=int, default=96)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--skip-extras", action="store_true")
+    ap.add_argument("--profile-table", default=None,
+                    help="with --profile-once batch: the shape table to use instead of autotuning, as "
+                         "'32:32x1,64:32x2,128:64x4,256:64x4' (bucket bound m: threads x columns per thread)")
     ap.add_argument("--served-requests", type=int, default=1500)
     ap.add_argument("--profile-once", default=None,
                     choices=["batch", "auction", "n16384", "n8192", "n16384dense", "n8192dense", "sinkhorn16384",
@@ -694,9 +697,15 @@ def main():
         ctx.close()
         return
     if args.profile_once:
-        # the timed configuration: tuned table, OT_AUTO; the three calls sit
-        # in an NVTX range "timed" for ncu --nvtx-include
-        ot.ot_autotune(ctx, dC, ot.OT_AUTO, repeats=1)
+        # the timed configuration: tuned table (or the one given), OT_AUTO;
+        # the three calls sit in an NVTX range "timed" for ncu --nvtx-include
+        if args.profile_table:
+            for ent in args.profile_table.split(","):
+                mb, shape = ent.split(":")
+                tpi, kk = shape.split("x")
+                ot.ot_tune_set(ctx, ot.OT_KM, int(mb), int(tpi), int(kk))
+        else:
+            ot.ot_autotune(ctx, dC, ot.OT_AUTO, repeats=1)
         a = ot.BatchArgs(dC)
         ot.ot_assign_solve_batched(ctx, a, ot.OT_AUTO, stream)
         torch.cuda.synchronize()
@@ -706,6 +715,12 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         assert (a.status.cpu().numpy() == 0).all()
+        # the launches of the timed solves (kernel and instances), which key
+        # the per-launch counts committed from a capture of this run
+        print(json.dumps({"profile_once": "batch", "launches": [
+            {"kernel": "group_kernel<%d, %d, %s>" % (L["threads_per_instance"], L["cols_per_thread"],
+                                                     {0: "KM", 1: "BKM"}.get(L["algo"], "AUCTION")),
+             "instances": L["instances"]} for L in ot.ot_last_call_launches(ctx)]}), flush=True)
         ctx.close()
         return
     h2d_bytes = sum(C.nbytes for C in Cs)
