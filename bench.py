@@ -705,7 +705,7 @@ def main():
                 tpi, kk = shape.split("x")
                 ot.ot_tune_set(ctx, ot.OT_KM, int(mb), int(tpi), int(kk))
         else:
-            ot.ot_autotune(ctx, dC, ot.OT_AUTO, repeats=1)
+            ot.ot_autotune(ctx, dC, ot.OT_AUTO, repeats=3)
         a = ot.BatchArgs(dC)
         ot.ot_assign_solve_batched(ctx, a, ot.OT_AUTO, stream)
         torch.cuda.synchronize()
@@ -729,7 +729,7 @@ def main():
 
     # autotune shape and algorithm (KM or batched KM) per size bucket on
     # this batch; OT_AUTO then uses the faster exact algorithm per bucket
-    ot.ot_autotune(ctx, dC, ot.OT_AUTO, repeats=1)
+    ot.ot_autotune(ctx, dC, ot.OT_AUTO, repeats=3)
     algo = ot.OT_AUTO
     tuned = {m: ot.ot_tune_lookup(ctx, ot.OT_AUTO, m) for m in (32, 64, 128, 256)}
     args_dev = ot.BatchArgs(dC)

@@ -1113,8 +1113,6 @@ int ot_autotune(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* 
     if (cudaError_t e = launch_pack(dinst, nullptr, k, s); e != cudaSuccess) return ctx_cuda(ctx, e, "autotune pack");
   }
   FILE* tf = ctx->tune_file.empty() ? nullptr : std::fopen(ctx->tune_file.c_str(), "a");
-  // per (algorithm, bucket): every shape timed alone, for the joint stage
-  std::map<std::pair<int, int>, std::vector<std::pair<int, float>>> alone;
   for (auto& kv : byb) {
     std::vector<int>& idx = kv.second;
     int nmax = 0, mmax = 0;
@@ -1150,7 +1148,6 @@ int ot_autotune(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* 
           cudaEventElapsedTime(&ms, e0, e1);
           if (r > 0) tmin = std::min(tmin, ms);  // first run warms up
         }
-        if (ok) alone[{a, kv.first}].emplace_back(sh, tmin);
         if (ok && tmin < best_ms) { best_ms = tmin; best = sh; }
       }
       if (best >= 0) {
@@ -1165,100 +1162,6 @@ int ot_autotune(ot_ctx* ctx, int32_t k, const int32_t* const* C, const int64_t* 
     if (algo == OT_AUTO && best_algo >= 0) {
       ctx->auto_algo[kv.first] = best_algo;
       if (tf) std::fprintf(tf, "{\"auto\": %d, \"bucket_mmax\": %d, \"ms\": %.4f}\n", best_algo, 32 << kv.first, best_algo_ms);
-    }
-  }
-  // Joint stage.  A batched solve runs the buckets at once (one launch per
-  // algorithm and shape, the instances of every bucket that shares it
-  // together, on the fork streams), so the shape fastest for a bucket alone
-  // need not be fastest beside the others.  Coordinate descent, largest
-  // bucket first, over each bucket's shapes within 25 % of its best time
-  // alone; a change is kept when the whole batch gets at least 1 % faster.
-  if (byb.size() >= 2) {
-    auto algo_of = [&](int b) { return algo == OT_AUTO ? ctx->auto_algo[b] : int(algo); };
-    // the buckets timed alone (shape indices in the table)
-    auto timed_b = [&](int b) {
-      const int a = algo_of(b);
-      return (a == kAlgoKM || a == kAlgoBKM) && alone.count({a, b}) && ctx->table[a][b] >= 0 &&
-             ctx->table[a][b] < num_group_shapes();
-    };
-    auto joint_ms = [&]() -> float {
-      std::map<int, std::vector<int>> groups;  // algorithm * 64 + shape -> instances
-      for (auto& kv : byb) {
-        if (!timed_b(kv.first)) continue;
-        const int a = algo_of(kv.first);
-        std::vector<int>& g = groups[a * 64 + ctx->table[a][kv.first]];
-        g.insert(g.end(), kv.second.begin(), kv.second.end());
-      }
-      std::vector<int32_t> ord;
-      std::vector<int> offs;
-      for (auto& gk : groups) {
-        std::vector<int>& g = gk.second;
-        std::sort(g.begin(), g.end(), [&](int x, int y) {
-          const long long wx = (long long)n[x] * m[x], wy = (long long)n[y] * m[y];
-          return wx != wy ? wx > wy : x < y;
-        });
-        offs.push_back(int(ord.size()));
-        ord.insert(ord.end(), g.begin(), g.end());
-      }
-      cudaMemcpyAsync(dorder, ord.data(), sizeof(int32_t) * ord.size(), cudaMemcpyHostToDevice, s);
-      float best_t = 1e30f;
-      for (int r = 0; r < 4; ++r) {
-        cudaMemsetAsync(dwork, 0, sizeof(int) * groups.size(), s);
-        cudaEventRecord(e0, s);
-        cudaEventRecord(ctx->fork_ev, s);
-        int gi = 0;
-        bool ok = true;
-        for (auto& gk : groups) {
-          const int a = gk.first / 64, sh = gk.first % 64;
-          int nmx = 0, mmx = 0;
-          for (int t : gk.second) { nmx = std::max(nmx, n[t]); mmx = std::max(mmx, m[t]); }
-          cudaStream_t bs = ctx->bstreams[gi % kForkStreams];
-          cudaStreamWaitEvent(bs, ctx->fork_ev, 0);
-          if (group_smem_bytes(group_shape(sh), a, nmx, mmx) > group_smem_limit() ||
-              launch_group(group_shape(sh), a, dinst, dorder + offs[gi], int(gk.second.size()), dwork + gi, nmx, mmx,
-                           ctx->max_group_ctas, bs) != cudaSuccess) {
-            cudaGetLastError();
-            ok = false;
-          }
-          ++gi;
-        }
-        for (int x = 0; x < std::min(gi, kForkStreams); ++x) {
-          cudaEventRecord(ctx->join_ev[x], ctx->bstreams[x]);
-          cudaStreamWaitEvent(s, ctx->join_ev[x], 0);
-        }
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        if (!ok) return 1e30f;
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (r > 0) best_t = std::min(best_t, ms);  // first run warms up
-      }
-      return best_t;
-    };
-    std::vector<std::pair<float, int>> order_b;  // (best time alone, bucket), largest first
-    for (auto& kv : byb) {
-      if (!timed_b(kv.first)) continue;
-      const auto it = alone.find({algo_of(kv.first), kv.first});
-      float bt = 1e30f;
-      for (auto& st : it->second) bt = std::min(bt, st.second);
-      order_b.emplace_back(bt, kv.first);
-    }
-    std::sort(order_b.rbegin(), order_b.rend());
-    float cur = joint_ms();
-    for (auto& ob : order_b) {
-      const int b = ob.second, a = algo_of(b);
-      const int keep = ctx->table[a][b];
-      for (auto& st : alone[{a, b}]) {
-        if (st.first == ctx->table[a][b] || st.second > 1.25f * ob.first) continue;
-        const int prev = ctx->table[a][b];
-        ctx->table[a][b] = st.first;
-        const float tj = joint_ms();
-        if (tj < 0.99f * cur) cur = tj;
-        else ctx->table[a][b] = prev;
-      }
-      if (tf && ctx->table[a][b] != keep)
-        std::fprintf(tf, "{\"algo\": %d, \"bucket_mmax\": %d, \"tpi\": %d, \"k\": %d, \"joint_ms\": %.4f}\n", a,
-                     32 << b, group_shape(ctx->table[a][b]).tpi, group_shape(ctx->table[a][b]).k, cur);
     }
   }
   if (tf) std::fclose(tf);
