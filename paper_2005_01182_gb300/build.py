@@ -1,7 +1,9 @@
 """Build libotassign.so in-tree for sm_103a (nvcc, no cmake).
 
 Every ``csrc/*.cu`` file is compiled to an object in parallel, then linked
-with the shared CUDA runtime into ``paper_2005_01182_gb300/lib/libotassign.so``.
+with the shared CUDA runtime into ``paper_2005_01182_gb300/lib/libotassign.so``;
+``client/served_client.cpp`` (a host-only client of the serving entry
+points, used by the served benchmark) becomes ``lib/libotclient.so``.
 Objects are rebuilt only when a source or header is newer.
 """
 from __future__ import annotations
@@ -19,6 +21,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libotassign.so")
+CLIENT_SRC = os.path.join(PKG, "client", "served_client.cpp")
+CLIENT_LIB = os.path.join(LIBDIR, "libotclient.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -66,6 +70,14 @@ def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
         tmp = LIB + f".{os.getpid()}.tmp"
         run([nvcc(), *ARCH, "-shared", "-cudart=shared", "-o", tmp, *objs, "-lpthread"])
         os.replace(tmp, LIB)
+    # the serving client (host code only, calls the library's C-ABI)
+    hdr_c = max(os.path.getmtime(CLIENT_SRC), os.path.getmtime(os.path.join(INCLUDE, "otassign.h")),
+                os.path.getmtime(LIB))
+    if not os.path.exists(CLIENT_LIB) or os.path.getmtime(CLIENT_LIB) < hdr_c:
+        tmp = CLIENT_LIB + f".{os.getpid()}.tmp"
+        run([os.environ.get("CXX", "g++"), "-O2", "-std=c++17", "-shared", "-fPIC", "-I", INCLUDE, CLIENT_SRC,
+             "-o", tmp, "-L", LIBDIR, "-lotassign", "-Wl,-rpath,$ORIGIN", "-lpthread"])
+        os.replace(tmp, CLIENT_LIB)
     return LIB
 
 

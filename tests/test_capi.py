@@ -33,3 +33,15 @@ def test_no_cpu_fallback_in_product():
         txt = f.read_text()
         assert not re.search(r"^\s*(import|from)\s+oracle\b", txt, re.M), f
         assert "ot_oracle" not in txt and "liboracle" not in txt, f
+
+
+def test_serving_client_library_builds_and_exports_replay(lib_path):
+    """The host-only serving client that the served benchmark drives is built
+    beside the library, links against it and exports its replay entry."""
+    from paper_2005_01182_gb300 import build
+    lib = ctypes.CDLL(build.CLIENT_LIB)
+    assert hasattr(lib, "otc_replay")
+    # argument checks return before any serving call
+    lib.otc_replay.restype = ctypes.c_int
+    total = ctypes.c_double()
+    assert lib.otc_replay(None, 0, None, None, None, 0, None, 1, 0, None, None, ctypes.byref(total)) == -1

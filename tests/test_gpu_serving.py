@@ -317,3 +317,49 @@ def test_completion_query_returns_each_request_once(oracle_mod, lib_path):
     finally:
         served.close()
         ref.close()
+
+
+def test_native_client_replay_matches_solo(lib_path):
+    """The native serving client (lib/libotclient.so) replays a stream through
+    submit / completed / poll: at once with a window of 8 outstanding
+    requests, then on Poisson arrival times; every collected cost equals the
+    matrix's solo solve and every request completes after it arrives."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import ctypes
+    from paper_2005_01182_gb300 import build
+    client = ctypes.CDLL(build.CLIENT_LIB)
+    client.otc_replay.restype = ctypes.c_int
+    client.otc_replay.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                  ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    reqs = W.served_requests(12, rate_per_s=1.0, lo=16, hi=600, seed=31)
+    mats = [torch.from_numpy(C).pin_memory() for _, C in reqs]
+    nreq = len(mats)
+    ref = ot.Context()
+    try:
+        b = ot.ot_assign_solve_batched(ref, [m.cuda() for m in mats], ot.OT_KM)
+        torch.cuda.synchronize()
+        solo = b.cost.cpu().numpy()
+    finally:
+        ref.close()
+    cptr = (ctypes.c_void_p * nreq)(*[m.data_ptr() for m in mats])
+    n_arr = np.array([m.shape[0] for m in mats], dtype=np.int32)
+    m_arr = np.array([m.shape[1] for m in mats], dtype=np.int32)
+    nstream = 40
+    for arrivals, window in ((np.zeros(nstream), 8), (np.cumsum(np.full(nstream, 2e-4)), nstream)):
+        arrivals = np.ascontiguousarray(arrivals, dtype=np.float64)
+        served = ot.Context(hbm_budget_bytes=256 << 20)
+        try:
+            done = np.zeros(nstream, dtype=np.float64)
+            cost = np.zeros(nstream, dtype=np.int64)
+            total = ctypes.c_double()
+            rc = client.otc_replay(served.h, nreq, cptr, n_arr.ctypes.data, m_arr.ctypes.data, nstream,
+                                   arrivals.ctypes.data, window, ot.OT_KM, done.ctypes.data, cost.ctypes.data,
+                                   ctypes.byref(total))
+            assert rc == 0
+            np.testing.assert_array_equal(cost, solo[np.arange(nstream) % nreq])
+            assert (done >= arrivals).all() and total.value >= done.max()
+            assert ot.ot_serving_counters(served)["completed"] == nstream
+        finally:
+            served.close()
