@@ -532,6 +532,15 @@ void ServeState::loop() {
     }
     launch_ready();
     reclaim_cancelled();
+    // requests collected by poll alone stay in the completion list until a
+    // completion query passes over them: keep the list bounded by the live
+    // requests for clients that never call it
+    if (watch.size() > 2 * reqs.size() + 1024) {
+      size_t keep = 0;
+      for (const uint64_t t : watch)
+        if (reqs.count(t)) watch[keep++] = t;
+      watch.resize(keep);
+    }
     // published requests still unfinished while no grid is resident
     if (!plive.empty()) {
       std::vector<uint64_t> keep;
